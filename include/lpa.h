@@ -1,0 +1,180 @@
+/*
+ * lpa.h -- C ABI of the GB300 (sm_103a) label-propagation library.
+ *
+ * Community detection by label propagation (LPA, Sec. 3.3, Eq. 3) with the
+ * memory-efficient label choice of arxiv 2411.19901: a k-slot weighted Misra-Gries
+ * sketch per vertex (Sec. 4.1-4.4, Alg. 1-2), the weighted Boyer-Moore variant
+ * (Sec. 4.7, Alg. 3) and an exact per-vertex table mode (the ν-LPA baseline, Sec. 4,
+ * Fig. 1), plus modularity (Sec. 3.2, Eq. 1).
+ *
+ * Conventions for every entry point:
+ *  - Graphs are CSR: offsets int64[n+1] (offsets[0] = 0, non-decreasing,
+ *    offsets[n] = m), indices int32[m] in [0, n), weights fp32[m] finite and >= 0, or
+ *    NULL for unit weights.  The graph must be symmetric (w_ij = w_ji, Sec. 3); this is
+ *    not checked.  Self-loops are allowed: the sweep skips them (the scan of Alg. 1
+ *    skips j = i), modularity counts them once as stored.  Edges of weight 0 carry no
+ *    vote.  n < 2^31, m < 2^62.
+ *  - Pointers are DEVICE memory owned by the caller unless marked "host".  The library
+ *    frees nothing it did not allocate.
+ *  - Calls are ordered on the caller's stream (lpa_options.stream; NULL = the legacy
+ *    default stream) and return after the stream work they issued has finished.
+ *  - Labels are int32 in [0, n): the initial label of vertex i is i (Alg. 1, `lpa`),
+ *    or the caller's labels_in.
+ *  - Results are deterministic: labels and per-iteration change counts do not depend
+ *    on kernel shapes, launch order or the GPU's scheduling.  Iterations are
+ *    synchronous: iteration l reads only the labels of iteration l-1.
+ *  - Errors return a negative lpa_status, leave the outputs unspecified and set a
+ *    thread-local message (lpa_last_error).  Without LPA_VALIDATE, an invalid graph
+ *    (an index outside [0, n), offsets that are not monotone) is undefined behaviour.
+ */
+#ifndef LPA_H
+#define LPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Label-choice rule.  LPA_EXACT: argmax of Eq. 3 (all neighbour labels).  LPA_MG: the
+ * heaviest candidate of a k-slot weighted Misra-Gries sketch (Sec. 4.1, single scan of
+ * Sec. 4.4).  LPA_BM: the weighted Boyer-Moore candidate (Sec. 4.7). */
+typedef enum { LPA_EXACT = 0, LPA_MG = 1, LPA_BM = 2 } lpa_mode;
+
+typedef enum {
+  LPA_OK = 0,
+  LPA_EINVAL = -1,        /* bad argument or (with LPA_VALIDATE) malformed graph */
+  LPA_ENOMEM = -2,        /* device allocation failed or workspace too small */
+  LPA_ECUDA = -3,         /* a CUDA runtime call failed (message in lpa_last_error) */
+  LPA_ETIMEOUT = -4,      /* a bounded device wait gave up */
+  LPA_EUNSUPPORTED = -5,  /* valid but not built (e.g. k not a power of two) */
+  LPA_EINTERNAL = -6      /* internal consistency check failed */
+} lpa_status;
+
+/* Flags for lpa_options.flags. */
+#define LPA_VALIDATE 0x1u /* check the CSR (and labels_in) on the device first */
+#define LPA_TIMING 0x2u   /* time the sweep and binning kernels with CUDA events */
+
+/* Largest max_iter accepted; lpa_stats.changed has this many entries. */
+#define LPA_MAX_ITER 1024
+
+/* Per-call statistics (HOST struct, filled on success). */
+typedef struct {
+  int32_t iterations;               /* sweeps performed */
+  int32_t converged;                /* 1 if dN/N < tol stopped the run (Alg. 1) */
+  int64_t changed[LPA_MAX_ITER];    /* dN of each performed sweep */
+  int64_t edges_scanned;            /* CSR positions read by the sweeps */
+  double seconds;                   /* host wall time of the call */
+  double sweep_ms;                  /* device time of all sweeps (LPA_TIMING) */
+  double setup_ms;                  /* device time of the degree binning (LPA_TIMING) */
+  int64_t sweep_launches;           /* sweeps that did work (== iterations) */
+  size_t device_bytes;              /* device workspace bytes used */
+  int32_t chunks;                   /* CTA work units of the binned graph */
+  int32_t hubs;                     /* vertices swept by a whole CTA */
+} lpa_stats;
+
+/* Options.  Call lpa_options_init first; it sets the paper's defaults (Sec. 5.1.2). */
+typedef struct {
+  int32_t pl_period;        /* rho: pick-less every rho iterations from the first;
+                               0 = never (Sec. 4.5).  Default 8. */
+  int32_t leaf_e0;          /* e0: rows shorter than 2*e0 are one sequential sketch;
+                               longer rows are split into L(d) partial sketches.
+                               Default 64. */
+  int32_t leaf_max;         /* Lmax: most partial sketches per row, power of two
+                               <= 256.  Default 256. */
+  uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING.  Default LPA_VALIDATE. */
+  const int32_t* labels_in; /* device, n labels in [0, n) to start from; NULL = C[i]=i */
+  void* stream;             /* cudaStream_t; NULL = legacy default stream */
+  void* workspace;          /* device scratch of workspace_bytes bytes, 256-byte
+                               aligned; NULL = allocated and freed by the call */
+  size_t workspace_bytes;
+} lpa_options;
+
+/* Leaf partition used by the sketches (fixed, so the result never depends on launch
+ * shapes): a row of d CSR positions has L(d) = 1 if d < 2*e0, else
+ * min(Lmax, largest power of two p with p*e0 <= d) leaves; leaf l covers positions
+ * [floor(l*d/L), floor((l+1)*d/L)) in CSR order and folds them into an empty sketch;
+ * leaves merge by the stride-doubling tree S[l] <- merge(S[l], S[l+s]), s = 1, 2, ...,
+ * where merge(A, B) accumulates B's occupied slots into A in slot order (partial
+ * sketches merged into S[0], Sec. 4.3).  MG is clamped: when no slot matches and none
+ * is free, all slots and the incoming weight drop by min(w, smallest slot) and a
+ * remainder takes the lowest free slot (Sec. 4.1).  Ties go to the smallest label. */
+
+void lpa_options_init(lpa_options* opt);
+
+/* Run LPA to convergence (Alg. 1, `lpa`): at most max_iter (<= LPA_MAX_ITER)
+ * synchronous sweeps; pick-less in iteration l iff rho > 0 and l mod rho == 0; stop
+ * after a non-pick-less sweep with (double)dN / n < tol.  k: MG slots, one of 1, 2, 4,
+ * 8, 16, 32 (ignored for EXACT and BM).  labels_out: device int32[n]; it may equal
+ * labels_in.  stats: host, may be NULL.  Default options. */
+lpa_status lpa_detect(const int64_t* offsets, const int32_t* indices, const float* weights,
+                      int32_t n, int64_t m, lpa_mode mode, int32_t k, double tol,
+                      int32_t max_iter, int32_t* labels_out, lpa_stats* stats);
+
+/* lpa_detect with explicit options (opt may be NULL for the defaults). */
+lpa_status lpa_detect_ex(const int64_t* offsets, const int32_t* indices,
+                         const float* weights, int32_t n, int64_t m, lpa_mode mode,
+                         int32_t k, double tol, int32_t max_iter, int32_t* labels_out,
+                         lpa_stats* stats, const lpa_options* opt);
+
+/* lpa_detect_ex for a graph held in HOST memory: offsets/indices/weights and
+ * labels_out are host pointers (page-locked memory gives the fastest copies); the call
+ * copies the graph to the device, runs, and copies the labels back.  opt->labels_in
+ * and opt->workspace, if set, are device pointers as usual. */
+lpa_status lpa_detect_host(const int64_t* offsets, const int32_t* indices,
+                           const float* weights, int32_t n, int64_t m, lpa_mode mode,
+                           int32_t k, double tol, int32_t max_iter, int32_t* labels_out,
+                           lpa_stats* stats, const lpa_options* opt);
+
+/* Modularity of labels (device int32[n], values in [0, n)), Eq. 1:
+ * Q = sum_c [sigma_c / 2m - (Sigma_c / 2m)^2] with 2m the sum of all CSR weights,
+ * sigma_c the weight of entries (i, j) with C_i = C_j = c and Sigma_c the summed
+ * weighted degree of c's vertices; fp64 accumulation; Q = 0 when 2m = 0.
+ * q_out: host. */
+lpa_status lpa_modularity(const int64_t* offsets, const int32_t* indices,
+                          const float* weights, int32_t n, int64_t m, const int32_t* labels,
+                          double* q_out);
+
+/* lpa_modularity with options (stream, workspace, LPA_VALIDATE; opt may be NULL). */
+lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices,
+                             const float* weights, int32_t n, int64_t m,
+                             const int32_t* labels, double* q_out, const lpa_options* opt);
+
+/* Device workspace an lpa_detect_ex call needs (an upper bound for any graph with these
+ * sizes); lpa_modularity_ex needs lpa_modularity_workspace_size(n). */
+size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k);
+size_t lpa_modularity_workspace_size(int32_t n);
+
+/* ---- Plans: bin a graph once, then run sweeps or whole runs on it. ---------------
+ * A plan keeps device pointers to the caller's graph (which must outlive it) and its
+ * own workspace.  lpa_plan_create performs the degree binning on the device. */
+typedef struct lpa_plan_s* lpa_plan;
+
+lpa_status lpa_plan_create(const int64_t* offsets, const int32_t* indices,
+                           const float* weights, int32_t n, int64_t m, lpa_mode mode,
+                           int32_t k, const lpa_options* opt, lpa_plan* plan_out);
+
+/* One synchronous sweep (Alg. 1, `lpaMove`): c_next[i] = the label vertex i chooses
+ * from c_prev, committed only if it differs and, when pick_less != 0, is smaller.
+ * c_prev and c_next are device int32[n] and must not overlap.  dn_out (host, may be
+ * NULL) receives dN; with dn_out == NULL the call does not wait for the sweep. */
+lpa_status lpa_plan_sweep(lpa_plan plan, const int32_t* c_prev, int32_t* c_next,
+                          int32_t pick_less, int64_t* dn_out);
+
+/* A whole run on the plan's graph (as lpa_detect_ex after binning). */
+lpa_status lpa_plan_run(lpa_plan plan, double tol, int32_t max_iter, int32_t* labels_out,
+                        lpa_stats* stats);
+
+lpa_status lpa_plan_destroy(lpa_plan plan);
+
+const char* lpa_status_string(lpa_status s);
+/* Message of the last failed call on this host thread ("" if none). */
+const char* lpa_last_error(void);
+/* Library version string. */
+const char* lpa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPA_H */

@@ -1,0 +1,598 @@
+// lpa_api.cu -- the C ABI declared in include/lpa.h: argument checks, workspace layout,
+// plans (degree binning once per graph) and the iteration driver of Alg. 1 (`lpa`).
+//
+// The driver never waits on the host between iterations: it enqueues max_iter
+// {sweep, convergence test} pairs; once the on-device test has fired, later sweeps exit
+// on their first instruction.  The host synchronises once, at the end, to read the
+// statistics.
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lpa.h"
+#include "lpa_internal.cuh"
+
+using namespace lpa;
+
+namespace {
+
+thread_local std::string g_err;
+
+lpa_status fail(lpa_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+lpa_status fail(lpa_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define LPA_CUDA(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+  } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout of a plan; offsets in bytes from the workspace base.
+struct Layout {
+  size_t state, dn, tmp, cv0, cv1, hubs, hub_tab, seg, tab_keys, tab_vals, total_fixed, total;
+};
+
+Layout layout(int64_t n, int64_t m, int mode, int64_t tab_slots) {
+  Layout L{};
+  size_t o = 0;
+  L.state = o;
+  o = align256(o + sizeof(DevState));
+  L.dn = o;
+  o = align256(o + sizeof(unsigned long long) * LPA_MAX_ITER);
+  L.tmp = o;
+  o = align256(o + sizeof(int32_t) * (size_t)n);
+  L.cv0 = o;
+  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
+  L.cv1 = o;
+  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
+  L.hubs = o;
+  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
+  L.hub_tab = o;
+  o = align256(o + (mode == kExact ? sizeof(int64_t) * (size_t)(n + 1) : 0));
+  L.seg = o;
+  o = align256(o + 3 * sizeof(int64_t) * (size_t)(num_segments(n) + 1));
+  L.total_fixed = o;
+  L.tab_keys = o;
+  o = align256(o + sizeof(int32_t) * (size_t)tab_slots);
+  L.tab_vals = o;
+  o = align256(o + sizeof(float) * (size_t)tab_slots);
+  L.total = o;
+  (void)m;
+  return L;
+}
+
+bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
+
+}  // namespace
+
+struct lpa_plan_s {
+  const int64_t* off = nullptr;
+  const int32_t* idx = nullptr;
+  const float* w = nullptr;
+  int32_t n = 0;
+  int64_t m = 0;
+  int mode = kMG, k = 8;
+  int e0 = 64, lmax = 256, rho = 8;
+  uint32_t flags = 0;
+  const int32_t* labels_in = nullptr;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  char* tab_ws = nullptr;  // exact-mode hub tables when the library allocates
+  bool own_tab = false;
+  Layout lay{};
+  DevState* st = nullptr;
+  unsigned long long* dn = nullptr;
+  int32_t* tmp = nullptr;
+  int32_t *cv0 = nullptr, *cv1 = nullptr, *hubs = nullptr;
+  int64_t* hub_tab = nullptr;
+  int32_t* tab_keys = nullptr;
+  float* tab_vals = nullptr;
+  int64_t nchunks = 0, nhubs = 0, hub_edges = 0;
+  double setup_ms = 0.0;
+  std::vector<cudaEvent_t> events;  // timing pairs, created on demand
+  DevState* host_state = nullptr;   // page-locked mirrors
+  unsigned long long* host_dn = nullptr;
+};
+
+namespace {
+
+lpa_status check_graph_args(const int64_t* offsets, const int32_t* indices, int32_t n,
+                            int64_t m) {
+  if (n < 0) return fail(LPA_EINVAL, "n = %d is negative", n);
+  if (m < 0 || m >= ((int64_t)1 << 62)) return fail(LPA_EINVAL, "m = %lld out of range", (long long)m);
+  if (!offsets) return fail(LPA_EINVAL, "offsets is NULL");
+  if (m > 0 && !indices) return fail(LPA_EINVAL, "indices is NULL with m > 0");
+  return LPA_OK;
+}
+
+lpa_status ensure_events(lpa_plan_s* p, size_t count) {
+  while (p->events.size() < count) {
+    cudaEvent_t e;
+    LPA_CUDA(cudaEventCreate(&e));
+    p->events.push_back(e);
+  }
+  return LPA_OK;
+}
+
+lpa_status sweep_args(lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next, int pick_less,
+                      unsigned long long* dn, const int32_t* done, SweepArgs* a) {
+  a->off = p->off;
+  a->idx = p->idx;
+  a->w = p->w;
+  a->c_prev = c_prev;
+  a->c_next = c_next;
+  a->chunk_v0 = p->cv0;
+  a->chunk_v1 = p->cv1;
+  a->hubs = p->hubs;
+  a->hub_tab = p->hub_tab;
+  a->tab_keys = p->tab_keys;
+  a->tab_vals = p->tab_vals;
+  a->dn = dn;
+  a->done = done;
+  a->nchunks = (int32_t)p->nchunks;
+  a->nhubs = (int32_t)p->nhubs;
+  a->pick_less = pick_less;
+  a->e0 = p->e0;
+  a->lmax = p->lmax;
+  return LPA_OK;
+}
+
+void destroy_plan(lpa_plan_s* p) {
+  if (!p) return;
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->own_ws && p->ws) cudaFreeAsync(p->ws, p->stream);
+  if (p->own_tab && p->tab_ws) cudaFreeAsync(p->tab_ws, p->stream);
+  if (p->own_ws || p->own_tab) cudaStreamSynchronize(p->stream);
+  if (p->host_state) cudaFreeHost(p->host_state);
+  if (p->host_dn) cudaFreeHost(p->host_dn);
+  delete p;
+}
+
+lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const float* weights,
+                       int32_t n, int64_t m, lpa_mode mode, int32_t k, const lpa_options* opt,
+                       lpa_plan_s** out) {
+  *out = nullptr;
+  lpa_status s = check_graph_args(offsets, indices, n, m);
+  if (s != LPA_OK) return s;
+  if (mode != LPA_EXACT && mode != LPA_MG && mode != LPA_BM)
+    return fail(LPA_EINVAL, "unknown mode %d", (int)mode);
+  if (mode == LPA_MG && (k < 1 || k > 32)) return fail(LPA_EINVAL, "k = %d outside [1, 32]", k);
+  if (mode == LPA_MG && !valid_k(k))
+    return fail(LPA_EUNSUPPORTED, "k = %d: only 1, 2, 4, 8, 16, 32 are built", k);
+  lpa_options defaults;
+  lpa_options_init(&defaults);
+  const lpa_options& o = opt ? *opt : defaults;
+  if (o.pl_period < 0) return fail(LPA_EINVAL, "pl_period = %d is negative", o.pl_period);
+  if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
+  if (o.leaf_max < 1 || o.leaf_max > kMaxLeaves || (o.leaf_max & (o.leaf_max - 1)))
+    return fail(LPA_EINVAL, "leaf_max = %d must be a power of two in [1, %d]", o.leaf_max, kMaxLeaves);
+
+  lpa_plan_s* p = new lpa_plan_s();
+  p->off = offsets;
+  p->idx = indices;
+  p->w = weights;
+  p->n = n;
+  p->m = m;
+  p->mode = (int)mode;
+  p->k = mode == LPA_MG ? k : 1;
+  p->e0 = o.leaf_e0;
+  p->lmax = o.leaf_max;
+  p->rho = o.pl_period;
+  p->flags = o.flags;
+  p->labels_in = o.labels_in;
+  p->stream = (cudaStream_t)o.stream;
+
+  auto bail = [&](lpa_status st) {
+    destroy_plan(p);
+    return st;
+  };
+  cudaError_t ce = cudaMallocHost((void**)&p->host_state, sizeof(DevState));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_dn, sizeof(unsigned long long) * LPA_MAX_ITER);
+  if (ce != cudaSuccess)
+    return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
+
+  // workspace: fixed part now; exact-mode hub tables once binning knows their size
+  const int64_t tab_bound = p->mode == kExact ? 2 * m : 0;
+  p->lay = layout(n, m, p->mode, tab_bound);
+  if (o.workspace) {
+    if (o.workspace_bytes < p->lay.total)
+      return bail(fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, p->lay.total));
+    if (((uintptr_t)o.workspace & 255) != 0)
+      return bail(fail(LPA_EINVAL, "workspace is not 256-byte aligned"));
+    p->ws = (char*)o.workspace;
+    p->ws_bytes = o.workspace_bytes;
+  } else {
+    p->ws_bytes = p->lay.total_fixed;
+    ce = cudaMallocAsync((void**)&p->ws, p->ws_bytes, p->stream);
+    if (ce != cudaSuccess)
+      return bail(fail(LPA_ENOMEM, "cudaMallocAsync(%zu): %s", p->ws_bytes, cudaGetErrorString(ce)));
+    p->own_ws = true;
+  }
+  p->st = (DevState*)(p->ws + p->lay.state);
+  p->dn = (unsigned long long*)(p->ws + p->lay.dn);
+  p->tmp = (int32_t*)(p->ws + p->lay.tmp);
+  p->cv0 = (int32_t*)(p->ws + p->lay.cv0);
+  p->cv1 = (int32_t*)(p->ws + p->lay.cv1);
+  p->hubs = (int32_t*)(p->ws + p->lay.hubs);
+  p->hub_tab = p->mode == kExact ? (int64_t*)(p->ws + p->lay.hub_tab) : nullptr;
+  int64_t* seg = (int64_t*)(p->ws + p->lay.seg);
+  const int64_t nseg = num_segments(n);
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (p->flags & LPA_TIMING) {
+    lpa_status es = ensure_events(p, 2);
+    if (es != LPA_OK) return bail(es);
+    ev0 = p->events[0];
+    ev1 = p->events[1];
+    ce = cudaEventRecord(ev0, p->stream);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(ce)));
+  }
+  ce = launch_fill_i32((int32_t*)p->st, 0, sizeof(DevState) / 4, p->stream);
+  if (ce == cudaSuccess && (p->flags & LPA_VALIDATE))
+    ce = launch_validate(offsets, indices, weights, n, m, p->labels_in, &p->st->err, p->stream);
+  if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "validation launch: %s", cudaGetErrorString(ce)));
+  if (p->flags & LPA_VALIDATE) {
+    ce = cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->stream);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "validation: %s", cudaGetErrorString(ce)));
+    const int err = p->host_state->err;
+    if (err) {
+      return bail(fail(LPA_EINVAL, "invalid input:%s%s%s%s", (err & kErrOffsets) ? " offsets" : "",
+                       (err & kErrIndex) ? " index out of range" : "",
+                       (err & kErrWeight) ? " negative/non-finite weight" : "",
+                       (err & kErrLabels) ? " labels_in out of range" : ""));
+    }
+  }
+
+  BinArgs b{};
+  b.off = offsets;
+  b.n = n;
+  b.cap = p->mode == kExact ? kChunkCapExact : kChunkCap;
+  b.cost_floor = b.cap / kThreads;
+  b.e0 = p->e0;
+  b.lmax = p->lmax;
+  b.leaves = p->mode == kExact ? 0 : 1;
+  b.seg_chunks = seg;
+  b.seg_hubs = seg + (nseg + 1);
+  b.seg_hub_edges = seg + 2 * (nseg + 1);
+  b.chunk_v0 = p->cv0;
+  b.chunk_v1 = p->cv1;
+  b.hubs = p->hubs;
+  b.hub_tab = p->hub_tab;
+  if (n > 0) {
+    ce = launch_bin(b, p->st, p->stream, false);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->stream);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "binning: %s", cudaGetErrorString(ce)));
+    p->nchunks = p->host_state->nchunks;
+    p->nhubs = p->host_state->nhubs;
+    p->hub_edges = p->host_state->hub_edges;
+    if (p->nchunks + p->nhubs > 0x7fffffffLL || p->nchunks > n || p->nhubs > n)
+      return bail(fail(LPA_EINTERNAL, "binning produced %lld chunks and %lld hubs",
+                       (long long)p->nchunks, (long long)p->nhubs));
+    ce = launch_bin(b, p->st, p->stream, true);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "binning: %s", cudaGetErrorString(ce)));
+  }
+  if (p->mode == kExact && p->hub_edges > 0) {
+    const int64_t slots = 2 * p->hub_edges;
+    if (o.workspace) {
+      p->tab_keys = (int32_t*)(p->ws + p->lay.tab_keys);
+      p->tab_vals = (float*)(p->ws + p->lay.tab_vals);
+    } else {
+      const size_t kb = align256(sizeof(int32_t) * (size_t)slots);
+      ce = cudaMallocAsync((void**)&p->tab_ws, kb + sizeof(float) * (size_t)slots, p->stream);
+      if (ce != cudaSuccess)
+        return bail(fail(LPA_ENOMEM, "cudaMallocAsync(hub tables): %s", cudaGetErrorString(ce)));
+      p->own_tab = true;
+      p->tab_keys = (int32_t*)p->tab_ws;
+      p->tab_vals = (float*)(p->tab_ws + kb);
+    }
+  }
+  if (p->flags & LPA_TIMING) {
+    ce = cudaEventRecord(ev1, p->stream);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "timing: %s", cudaGetErrorString(ce)));
+    p->setup_ms = ms;
+  }
+  *out = p;
+  return LPA_OK;
+}
+
+lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels_out,
+                    lpa_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (max_iter < 0 || max_iter > LPA_MAX_ITER)
+    return fail(LPA_EINVAL, "max_iter = %d outside [0, %d]", max_iter, LPA_MAX_ITER);
+  if (!(tol == tol)) return fail(LPA_EINVAL, "tol is NaN");
+  if (p->n > 0 && !labels_out) return fail(LPA_EINVAL, "labels_out is NULL");
+  cudaStream_t s = p->stream;
+  const int32_t n = p->n;
+  if (n == 0) {  // nothing to do; matches the definition of convergence on an empty graph
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->converged = 1;
+      stats->device_bytes = p->ws_bytes;
+    }
+    return LPA_OK;
+  }
+  const bool timing = (p->flags & LPA_TIMING) != 0;
+  if (timing) {
+    lpa_status es = ensure_events(p, 2 + 2 * (size_t)max_iter);
+    if (es != LPA_OK) return es;
+  }
+  LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));  // done, iterations, converged, err
+  LPA_CUDA(launch_fill_u64(p->dn, 0ull, max_iter, s));
+  LPA_CUDA(launch_init_labels(labels_out, p->labels_in, n, s));
+  int32_t* buf[2] = {labels_out, p->tmp};
+  for (int l = 0; l < max_iter; ++l) {
+    const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
+    SweepArgs a{};
+    sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less, p->dn + l, &p->st->done, &a);
+    if (timing) LPA_CUDA(cudaEventRecord(p->events[2 + 2 * l], s));
+    LPA_CUDA(launch_sweep(p->mode, p->k, p->w != nullptr, a, s));
+    if (timing) LPA_CUDA(cudaEventRecord(p->events[3 + 2 * l], s));
+    LPA_CUDA(launch_converge(p->st, p->dn, l, pick_less, tol, n, s));
+  }
+  LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  if (max_iter > 0)
+    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn, sizeof(unsigned long long) * max_iter,
+                             cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaStreamSynchronize(s));
+  const int iters = p->host_state->iterations;
+  if (iters < 0 || iters > max_iter) return fail(LPA_EINTERNAL, "device reported %d iterations", iters);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = iters;
+    stats->converged = p->host_state->converged;
+    for (int l = 0; l < iters; ++l) stats->changed[l] = (int64_t)p->host_dn[l];
+    stats->edges_scanned = (int64_t)iters * p->m;
+    stats->sweep_launches = iters;
+    stats->device_bytes = p->ws_bytes + (p->own_tab ? (size_t)(2 * p->hub_edges) * 8 : 0);
+    stats->chunks = (int32_t)p->nchunks;
+    stats->hubs = (int32_t)p->nhubs;
+    stats->setup_ms = p->setup_ms;
+    if (timing) {
+      double tot = 0.0;
+      for (int l = 0; l < iters; ++l) {
+        float ms = 0.f;
+        LPA_CUDA(cudaEventElapsedTime(&ms, p->events[2 + 2 * l], p->events[3 + 2 * l]));
+        tot += ms;
+      }
+      stats->sweep_ms = tot;
+    }
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return LPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lpa_options_init(lpa_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->pl_period = 8;
+  opt->leaf_e0 = 64;
+  opt->leaf_max = 256;
+  opt->flags = LPA_VALIDATE;
+}
+
+size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k) {
+  (void)k;
+  if (n < 0 || m < 0) return 0;
+  return layout(n, m, (int)mode, mode == LPA_EXACT ? 2 * m : 0).total;
+}
+
+size_t lpa_modularity_workspace_size(int32_t n) {
+  if (n < 0) return 0;
+  return align256(sizeof(double) * (size_t)n) + align256(sizeof(double) * 3 * modularity_partials(n)) +
+         align256(sizeof(double) * 4) + align256(sizeof(DevState));
+}
+
+lpa_status lpa_plan_create(const int64_t* offsets, const int32_t* indices, const float* weights,
+                           int32_t n, int64_t m, lpa_mode mode, int32_t k, const lpa_options* opt,
+                           lpa_plan* plan_out) {
+  if (!plan_out) return fail(LPA_EINVAL, "plan_out is NULL");
+  return plan_create(offsets, indices, weights, n, m, mode, k, opt, plan_out);
+}
+
+lpa_status lpa_plan_sweep(lpa_plan p, const int32_t* c_prev, int32_t* c_next, int32_t pick_less,
+                          int64_t* dn_out) {
+  if (!p) return fail(LPA_EINVAL, "plan is NULL");
+  if (p->n == 0) {
+    if (dn_out) *dn_out = 0;
+    return LPA_OK;
+  }
+  if (!c_prev || !c_next) return fail(LPA_EINVAL, "c_prev/c_next is NULL");
+  const char* a0 = (const char*)c_prev;
+  const char* b0 = (const char*)c_next;
+  const size_t bytes = sizeof(int32_t) * (size_t)p->n;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(LPA_EINVAL, "c_prev and c_next overlap");
+  LPA_CUDA(launch_fill_u64(p->dn, 0ull, 1, p->stream));
+  SweepArgs a{};
+  sweep_args(p, c_prev, c_next, pick_less ? 1 : 0, p->dn, nullptr, &a);
+  LPA_CUDA(launch_sweep(p->mode, p->k, p->w != nullptr, a, p->stream));
+  if (dn_out) {
+    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             p->stream));
+    LPA_CUDA(cudaStreamSynchronize(p->stream));
+    *dn_out = (int64_t)p->host_dn[0];
+  }
+  return LPA_OK;
+}
+
+lpa_status lpa_plan_run(lpa_plan p, double tol, int32_t max_iter, int32_t* labels_out,
+                        lpa_stats* stats) {
+  if (!p) return fail(LPA_EINVAL, "plan is NULL");
+  return plan_run(p, tol, max_iter, labels_out, stats);
+}
+
+lpa_status lpa_plan_destroy(lpa_plan p) {
+  destroy_plan(p);
+  return LPA_OK;
+}
+
+lpa_status lpa_detect_ex(const int64_t* offsets, const int32_t* indices, const float* weights,
+                         int32_t n, int64_t m, lpa_mode mode, int32_t k, double tol,
+                         int32_t max_iter, int32_t* labels_out, lpa_stats* stats,
+                         const lpa_options* opt) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (max_iter < 0 || max_iter > LPA_MAX_ITER)
+    return fail(LPA_EINVAL, "max_iter = %d outside [0, %d]", max_iter, LPA_MAX_ITER);
+  lpa_plan_s* p = nullptr;
+  lpa_status s = plan_create(offsets, indices, weights, n, m, mode, k, opt, &p);
+  if (s != LPA_OK) return s;
+  s = plan_run(p, tol, max_iter, labels_out, stats);
+  destroy_plan(p);
+  if (s == LPA_OK && stats)
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s;
+}
+
+lpa_status lpa_detect(const int64_t* offsets, const int32_t* indices, const float* weights,
+                      int32_t n, int64_t m, lpa_mode mode, int32_t k, double tol, int32_t max_iter,
+                      int32_t* labels_out, lpa_stats* stats) {
+  return lpa_detect_ex(offsets, indices, weights, n, m, mode, k, tol, max_iter, labels_out, stats,
+                       nullptr);
+}
+
+lpa_status lpa_detect_host(const int64_t* offsets, const int32_t* indices, const float* weights,
+                           int32_t n, int64_t m, lpa_mode mode, int32_t k, double tol,
+                           int32_t max_iter, int32_t* labels_out, lpa_stats* stats,
+                           const lpa_options* opt) {
+  const auto t0 = std::chrono::steady_clock::now();
+  lpa_status s = check_graph_args(offsets, indices, n, m);
+  if (s != LPA_OK) return s;
+  if (n > 0 && !labels_out) return fail(LPA_EINVAL, "labels_out is NULL");
+  lpa_options o;
+  lpa_options_init(&o);
+  if (opt) o = *opt;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  char* dev = nullptr;
+  const size_t b_off = align256(sizeof(int64_t) * ((size_t)n + 1));
+  const size_t b_idx = align256(sizeof(int32_t) * (size_t)m);
+  const size_t b_w = weights ? align256(sizeof(float) * (size_t)m) : 0;
+  const size_t b_lab = align256(sizeof(int32_t) * (size_t)n);
+  LPA_CUDA(cudaMallocAsync((void**)&dev, b_off + b_idx + b_w + b_lab, st));
+  int64_t* d_off = (int64_t*)dev;
+  int32_t* d_idx = (int32_t*)(dev + b_off);
+  float* d_w = weights ? (float*)(dev + b_off + b_idx) : nullptr;
+  int32_t* d_lab = (int32_t*)(dev + b_off + b_idx + b_w);
+  cudaError_t ce = cudaMemcpyAsync(d_off, offsets, sizeof(int64_t) * ((size_t)n + 1),
+                                   cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && m > 0)
+    ce = cudaMemcpyAsync(d_idx, indices, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && weights && m > 0)
+    ce = cudaMemcpyAsync(d_w, weights, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, st);
+  if (ce != cudaSuccess) {
+    cudaFreeAsync(dev, st);
+    return fail(LPA_ECUDA, "host-to-device copy: %s", cudaGetErrorString(ce));
+  }
+  s = lpa_detect_ex(d_off, d_idx, d_w, n, m, mode, k, tol, max_iter, d_lab, stats, &o);
+  if (s == LPA_OK && n > 0) {
+    ce = cudaMemcpyAsync(labels_out, d_lab, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) s = fail(LPA_ECUDA, "device-to-host copy: %s", cudaGetErrorString(ce));
+  }
+  cudaFreeAsync(dev, st);
+  ce = cudaStreamSynchronize(st);
+  if (s == LPA_OK && ce != cudaSuccess) s = fail(LPA_ECUDA, "sync: %s", cudaGetErrorString(ce));
+  if (s == LPA_OK && stats)
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s;
+}
+
+lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices, const float* weights,
+                             int32_t n, int64_t m, const int32_t* labels, double* q_out,
+                             const lpa_options* opt) {
+  lpa_status s = check_graph_args(offsets, indices, n, m);
+  if (s != LPA_OK) return s;
+  if (!q_out) return fail(LPA_EINVAL, "q_out is NULL");
+  if (n > 0 && !labels) return fail(LPA_EINVAL, "labels is NULL");
+  lpa_options o;
+  lpa_options_init(&o);
+  if (opt) o = *opt;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int npart = modularity_partials(n);
+  const size_t need = lpa_modularity_workspace_size(n);
+  char* ws = (char*)o.workspace;
+  bool own = false;
+  if (ws) {
+    if (o.workspace_bytes < need) return fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, need);
+    if (((uintptr_t)ws & 255) != 0) return fail(LPA_EINVAL, "workspace is not 256-byte aligned");
+  } else {
+    LPA_CUDA(cudaMallocAsync((void**)&ws, need, st));
+    own = true;
+  }
+  double* sigma_c = (double*)ws;
+  double* partials = (double*)(ws + align256(sizeof(double) * (size_t)n));
+  double* out3 = (double*)((char*)partials + align256(sizeof(double) * 3 * npart));
+  DevState* dst = (DevState*)((char*)out3 + align256(sizeof(double) * 4));
+  double host_out[4] = {0, 0, 0, 0};
+  DevState host_st{};
+  cudaError_t ce = cudaSuccess;
+  if (o.flags & LPA_VALIDATE) {
+    ce = launch_fill_i32((int32_t*)dst, 0, sizeof(DevState) / 4, st);
+    if (ce == cudaSuccess) ce = launch_validate(offsets, indices, weights, n, m, labels, &dst->err, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&host_st, dst, sizeof(DevState), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess && host_st.err) {
+      if (own) cudaFreeAsync(ws, st);
+      cudaStreamSynchronize(st);
+      return fail(LPA_EINVAL, "invalid input (error bits 0x%x)", host_st.err);
+    }
+  }
+  if (ce == cudaSuccess) ce = launch_modularity(offsets, indices, weights, labels, n, sigma_c, partials, npart, out3, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_out, out3, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
+  if (own) cudaFreeAsync(ws, st);
+  cudaError_t ce2 = cudaStreamSynchronize(st);
+  if (ce == cudaSuccess) ce = ce2;
+  if (ce != cudaSuccess) return fail(LPA_ECUDA, "modularity: %s", cudaGetErrorString(ce));
+  *q_out = host_out[3];
+  return LPA_OK;
+}
+
+lpa_status lpa_modularity(const int64_t* offsets, const int32_t* indices, const float* weights,
+                          int32_t n, int64_t m, const int32_t* labels, double* q_out) {
+  return lpa_modularity_ex(offsets, indices, weights, n, m, labels, q_out, nullptr);
+}
+
+const char* lpa_status_string(lpa_status s) {
+  switch (s) {
+    case LPA_OK: return "ok";
+    case LPA_EINVAL: return "invalid argument";
+    case LPA_ENOMEM: return "out of device memory";
+    case LPA_ECUDA: return "CUDA error";
+    case LPA_ETIMEOUT: return "device wait timed out";
+    case LPA_EUNSUPPORTED: return "unsupported";
+    case LPA_EINTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* lpa_last_error(void) { return g_err.c_str(); }
+
+const char* lpa_version(void) { return "lpa-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,393 @@
+// lpa_setup.cu -- everything around the sweep: CSR validation, degree binning into
+// chunks and hubs, label initialisation, the on-device convergence test (Alg. 1, `lpa`),
+// and modularity (Eq. 1).
+#include "lpa_internal.cuh"
+
+namespace lpa {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+// ------------------------------------------------------------------ validation
+
+__global__ void validate_offsets_kernel(const int64_t* off, int32_t n, int64_t m, int32_t* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+    bool bad = false;
+    if (v == 0 && off[0] != 0) bad = true;
+    if (v == n && off[n] != m) bad = true;
+    if (v < n && off[v + 1] < off[v]) bad = true;
+    if (bad) atomicOr(err, kErrOffsets);
+  }
+}
+
+__global__ void validate_edges_kernel(const int32_t* idx, const float* w, int32_t n, int64_t m,
+                                      const int32_t* labels_in, int32_t* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int bits = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t j = idx[e];
+    if (j < 0 || j >= n) bits |= kErrIndex;
+    if (w) {
+      const float x = w[e];
+      if (!(x >= 0.f) || isinf(x)) bits |= kErrWeight;  // !(x >= 0) also catches NaN
+    }
+  }
+  if (labels_in)
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+      const int32_t c = labels_in[v];
+      if (c < 0 || c >= n) bits |= kErrLabels;
+    }
+  if (bits) atomicOr(err, bits);
+}
+
+// ------------------------------------------------------------------ binning
+
+// Greedy chunking of one segment of vertices.  A vertex is a hub if its row exceeds a
+// chunk (d > cap) or it has more leaves than a warp has lanes.  Other vertices join the
+// current chunk while its cost stays <= cap, with cost = max(d, floor * L, floor):
+// so a chunk holds <= cap edges and <= cap / floor = kThreads vertices and leaves.
+template <bool WRITE>
+__device__ void greedy_segment(const BinArgs& b, int64_t seg, int64_t& nch, int64_t& nhub,
+                               int64_t& hub_edges) {
+  const int64_t v_begin = seg * kSegment;
+  const int64_t v_end = min((int64_t)b.n, v_begin + kSegment);
+  int64_t ch_out = WRITE ? b.seg_chunks[seg] : 0;
+  int64_t hub_out = WRITE ? b.seg_hubs[seg] : 0;
+  int64_t tab_out = WRITE ? 2 * b.seg_hub_edges[seg] : 0;
+  nch = 0;
+  nhub = 0;
+  hub_edges = 0;
+  int64_t cur_start = -1, cur_cost = 0;
+  int64_t o_next = b.off[v_begin];
+  for (int64_t v = v_begin; v < v_end; ++v) {
+    const int64_t o = o_next;
+    o_next = b.off[v + 1];
+    const int64_t d = o_next - o;
+    const int L = b.leaves ? leaf_count(d, b.e0, b.lmax) : 1;
+    if (d > b.cap || L > kMaxWarpLeaves) {
+      if (cur_start >= 0) {
+        if (WRITE) {
+          b.chunk_v0[ch_out] = (int32_t)cur_start;
+          b.chunk_v1[ch_out] = (int32_t)v;
+          ++ch_out;
+        }
+        ++nch;
+        cur_start = -1;
+      }
+      if (WRITE) {
+        b.hubs[hub_out] = (int32_t)v;
+        if (b.hub_tab) b.hub_tab[hub_out] = tab_out;
+        ++hub_out;
+        tab_out += 2 * d;
+      }
+      ++nhub;
+      hub_edges += d;
+      continue;
+    }
+    int64_t cost = d;
+    if (cost < (int64_t)b.cost_floor * L) cost = (int64_t)b.cost_floor * L;
+    if (cur_start >= 0 && cur_cost + cost > b.cap) {
+      if (WRITE) {
+        b.chunk_v0[ch_out] = (int32_t)cur_start;
+        b.chunk_v1[ch_out] = (int32_t)v;
+        ++ch_out;
+      }
+      ++nch;
+      cur_start = -1;
+    }
+    if (cur_start < 0) {
+      cur_start = v;
+      cur_cost = 0;
+    }
+    cur_cost += cost;
+  }
+  if (cur_start >= 0) {
+    if (WRITE) {
+      b.chunk_v0[ch_out] = (int32_t)cur_start;
+      b.chunk_v1[ch_out] = (int32_t)v_end;
+    }
+    ++nch;
+  }
+}
+
+__global__ void bin_count_kernel(BinArgs b, int64_t nseg) {
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  int64_t c, h, he;
+  greedy_segment<false>(b, seg, c, h, he);
+  b.seg_chunks[seg] = c;
+  b.seg_hubs[seg] = h;
+  b.seg_hub_edges[seg] = he;
+}
+
+__global__ void bin_write_kernel(BinArgs b, int64_t nseg) {
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  int64_t c, h, he;
+  greedy_segment<true>(b, seg, c, h, he);
+}
+
+// Exclusive prefix sums of three int64 arrays (one block); totals go to the state.
+__global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t* b, int64_t* c,
+                                                             int64_t len, DevState* st) {
+  __shared__ int64_t sa[kScanThreads], sb[kScanThreads], sc[kScanThreads];
+  const int tid = threadIdx.x;
+  const int64_t per = (len + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = min(len, tid * per), hi = min(len, lo + per);
+  int64_t ta = 0, tb = 0, tc = 0;
+  for (int64_t i = lo; i < hi; ++i) {
+    ta += a[i];
+    tb += b[i];
+    tc += c[i];
+  }
+  sa[tid] = ta;
+  sb[tid] = tb;
+  sc[tid] = tc;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
+    int64_t xa = 0, xb = 0, xc = 0;
+    if (tid >= o) {
+      xa = sa[tid - o];
+      xb = sb[tid - o];
+      xc = sc[tid - o];
+    }
+    __syncthreads();
+    sa[tid] += xa;
+    sb[tid] += xb;
+    sc[tid] += xc;
+    __syncthreads();
+  }
+  int64_t ra = sa[tid] - ta, rb = sb[tid] - tb, rc = sc[tid] - tc;
+  for (int64_t i = lo; i < hi; ++i) {
+    const int64_t xa = a[i], xb = b[i], xc = c[i];
+    a[i] = ra;
+    b[i] = rb;
+    c[i] = rc;
+    ra += xa;
+    rb += xb;
+    rc += xc;
+  }
+  if (tid == kScanThreads - 1) {
+    st->nchunks = sa[tid];
+    st->nhubs = sb[tid];
+    st->hub_edges = sc[tid];
+  }
+}
+
+// ------------------------------------------------------------ driver helpers
+
+__global__ void init_labels_kernel(int32_t* c, const int32_t* labels_in, int32_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    c[v] = labels_in ? labels_in[v] : (int32_t)v;
+}
+
+// Convergence test after sweep l (Alg. 1): stop iff pick-less was off and dN/N < tau.
+__global__ void converge_kernel(DevState* st, const unsigned long long* dn, int l, int pick_less,
+                                double tol, int32_t n) {
+  if (threadIdx.x != 0 || st->done) return;
+  st->iterations = l + 1;
+  if (!pick_less && (double)dn[l] / (double)n < tol) {
+    st->done = 1;
+    st->converged = 1;
+  }
+}
+
+// Iteration l writes buffer (l+1) & 1; buffer 0 is the caller's output.
+__global__ void finalize_kernel(const DevState* st, int32_t* out, const int32_t* tmp, int32_t n) {
+  if ((st->iterations & 1) == 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    out[v] = tmp[v];
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int32_t value, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = value;
+}
+
+__global__ void fill_u64_kernel(unsigned long long* p, unsigned long long value, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = value;
+}
+
+// ------------------------------------------------------------------ modularity
+
+constexpr int kModThreads = 256;
+constexpr int kModBlocks = 152 * 8;
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Pass 1 (warp per vertex): K_i and intra-community weight; Sigma_c += K_i.
+__global__ void __launch_bounds__(kModThreads) modularity_rows_kernel(
+    const int64_t* off, const int32_t* idx, const float* w, const int32_t* labels, int32_t n,
+    double* sigma_c, double* partials) {
+  __shared__ double s_k[kModThreads / 32], s_in[kModThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kModThreads / 32);
+  double acc_k = 0.0, acc_in = 0.0;
+  for (int64_t v = (int64_t)blockIdx.x * (kModThreads / 32) + wid; v < n; v += nwarps) {
+    const int cv = labels[v];
+    double kv = 0.0, in = 0.0;
+    for (int64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
+      const double x = w ? (double)w[p] : 1.0;
+      kv += x;
+      if (labels[idx[p]] == cv) in += x;
+    }
+    kv = warp_sum(kv);
+    in = warp_sum(in);
+    if (lane == 0) {
+      if (kv != 0.0) atomicAdd(sigma_c + cv, kv);
+      acc_k += kv;
+      acc_in += in;
+    }
+  }
+  if (lane == 0) {
+    s_k[wid] = acc_k;
+    s_in[wid] = acc_in;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < kModThreads / 32; ++i) {
+      a += s_k[i];
+      b += s_in[i];
+    }
+    partials[3 * blockIdx.x + 0] = a;
+    partials[3 * blockIdx.x + 1] = b;
+  }
+}
+
+// Pass 2: sum over communities of Sigma_c^2.
+__global__ void __launch_bounds__(kModThreads) modularity_sq_kernel(const double* sigma_c, int32_t n,
+                                                                    double* partials) {
+  __shared__ double s[kModThreads / 32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kModThreads;
+  for (int64_t c = (int64_t)blockIdx.x * kModThreads + threadIdx.x; c < n; c += stride)
+    acc += sigma_c[c] * sigma_c[c];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < kModThreads / 32; ++i) a += s[i];
+    partials[3 * blockIdx.x + 2] = a;
+  }
+}
+
+// Fixed-order final reduction of the per-block partials.
+__global__ void modularity_final_kernel(const double* partials, int32_t npart, double* out3) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = 0; i < npart; ++i) {
+    a += partials[3 * i + 0];
+    b += partials[3 * i + 1];
+    c += partials[3 * i + 2];
+  }
+  out3[0] = a;
+  out3[1] = b;
+  out3[2] = c;
+  // Eq. 1: Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2
+  out3[3] = a > 0.0 ? b / a - c / (a * a) : 0.0;
+}
+
+__global__ void fill_f64_kernel(double* p, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = 0.0;
+}
+
+inline unsigned grid_for(int64_t work, int threads, unsigned cap = 152 * 16) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (unsigned)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int32_t n,
+                            int64_t m, const int32_t* labels_in, int32_t* err, cudaStream_t s) {
+  validate_offsets_kernel<<<grid_for((int64_t)n + 1, 256), 256, 0, s>>>(off, n, m, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  validate_edges_kernel<<<grid_for(m > n ? m : n, 256), 256, 0, s>>>(idx, w, n, m, labels_in, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const BinArgs& b, DevState* st, cudaStream_t s, bool write_pass) {
+  const int64_t nseg = num_segments(b.n);
+  if (nseg == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((nseg + 127) / 128);
+  if (!write_pass) {
+    bin_count_kernel<<<grid, 128, 0, s>>>(b, nseg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scan3_kernel<<<1, kScanThreads, 0, s>>>(b.seg_chunks, b.seg_hubs, b.seg_hub_edges, nseg, st);
+    return cudaGetLastError();
+  }
+  bin_write_kernel<<<grid, 128, 0, s>>>(b, nseg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  init_labels_kernel<<<grid_for(n, 256), 256, 0, s>>>(c, labels_in, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_converge(DevState* st, const unsigned long long* dn, int l, int pick_less,
+                            double tol, int32_t n, cudaStream_t s) {
+  converge_kernel<<<1, 32, 0, s>>>(st, dn, l, pick_less, tol, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp, int32_t n,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(st, out, tmp, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  fill_i32_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long value, int64_t count,
+                            cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  fill_u64_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  return cudaGetLastError();
+}
+
+int modularity_partials(int32_t n) {
+  (void)n;
+  return kModBlocks;
+}
+
+cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const float* w,
+                              const int32_t* labels, int32_t n, double* sigma_c, double* partials,
+                              int32_t npart, double* out3, cudaStream_t s) {
+  fill_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(sigma_c, n);
+  fill_f64_kernel<<<grid_for(3 * (int64_t)npart, 256), 256, 0, s>>>(partials, 3 * (int64_t)npart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    modularity_rows_kernel<<<npart, kModThreads, 0, s>>>(off, idx, w, labels, n, sigma_c, partials);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    modularity_sq_kernel<<<npart, kModThreads, 0, s>>>(sigma_c, n, partials);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  modularity_final_kernel<<<1, 32, 0, s>>>(partials, npart, out3);
+  return cudaGetLastError();
+}
+
+}  // namespace lpa

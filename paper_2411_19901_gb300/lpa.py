@@ -1,0 +1,322 @@
+"""Thin ctypes binding of the C ABI in ``include/lpa.h`` (``liblpa.so``).
+
+Argument marshalling only: every step of label propagation runs in the CUDA library.
+Functions carry the C names; pointer arguments accept a CUDA ``torch.Tensor`` (device
+pointers), a numpy array (host pointers, for ``lpa_detect_host``), a raw integer address,
+or None.  Streams default to PyTorch's current stream.  A missing library raises: there
+is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblpa.so")
+
+LPA_EXACT, LPA_MG, LPA_BM = 0, 1, 2
+MODES = {"exact": LPA_EXACT, "mg": LPA_MG, "bm": LPA_BM}
+LPA_VALIDATE = 0x1
+LPA_TIMING = 0x2
+LPA_MAX_ITER = 1024
+
+STATUS = {0: "LPA_OK", -1: "LPA_EINVAL", -2: "LPA_ENOMEM", -3: "LPA_ECUDA",
+          -4: "LPA_ETIMEOUT", -5: "LPA_EUNSUPPORTED", -6: "LPA_EINTERNAL"}
+
+
+class LpaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lpa_stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("changed", ctypes.c_int64 * LPA_MAX_ITER),
+        ("edges_scanned", ctypes.c_int64),
+        ("seconds", ctypes.c_double),
+        ("sweep_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("sweep_launches", ctypes.c_int64),
+        ("device_bytes", ctypes.c_size_t),
+        ("chunks", ctypes.c_int32),
+        ("hubs", ctypes.c_int32),
+    ]
+
+    def to_dict(self) -> dict:
+        it = int(self.iterations)
+        return {
+            "iterations": it,
+            "converged": bool(self.converged),
+            "changed": [int(x) for x in self.changed[:it]],
+            "edges_scanned": int(self.edges_scanned),
+            "seconds": float(self.seconds),
+            "sweep_ms": float(self.sweep_ms),
+            "setup_ms": float(self.setup_ms),
+            "sweep_launches": int(self.sweep_launches),
+            "device_bytes": int(self.device_bytes),
+            "chunks": int(self.chunks),
+            "hubs": int(self.hubs),
+        }
+
+
+class lpa_options(ctypes.Structure):
+    _fields_ = [
+        ("pl_period", ctypes.c_int32),
+        ("leaf_e0", ctypes.c_int32),
+        ("leaf_max", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("labels_in", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIG = {
+    "lpa_options_init": (None, [ctypes.POINTER(lpa_options)]),
+    "lpa_detect": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                  ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "lpa_detect_ex": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P,
+                                     _P]),
+    "lpa_detect_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P,
+                                       _P]),
+    "lpa_modularity": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, _P]),
+    "lpa_modularity_ex": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                         _P]),
+    "lpa_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                             ctypes.c_int32]),
+    "lpa_modularity_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "lpa_plan_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    "lpa_plan_run": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "lpa_plan_destroy": (ctypes.c_int, [_P]),
+    "lpa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lpa_last_error": (ctypes.c_char_p, []),
+    "lpa_version": (ctypes.c_char_p, []),
+}
+
+EXPORTED = tuple(_SIG)
+
+
+def load(path: str = LIB_PATH):
+    """Load ``liblpa.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -m paper_2411_19901_gb300.build); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIG.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = load().lpa_last_error().decode(errors="replace")
+        raise LpaError(status, msg)
+
+
+def _ptr(x):
+    """Device or host address of x (tensor, numpy array, int, None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("numpy arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _mode(mode):
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def lpa_options_init() -> lpa_options:
+    o = lpa_options()
+    load().lpa_options_init(ctypes.byref(o))
+    return o
+
+
+def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=False,
+                 labels_in=None, stream=None, workspace=None, workspace_bytes=0) -> lpa_options:
+    o = lpa_options_init()
+    o.pl_period = pl_period
+    o.leaf_e0 = leaf_e0
+    o.leaf_max = leaf_max
+    o.flags = (LPA_VALIDATE if validate else 0) | (LPA_TIMING if timing else 0)
+    o.labels_in = _ptr(labels_in)
+    o.stream = _stream_handle(stream)
+    if workspace is not None:
+        o.workspace = _ptr(workspace)
+        o.workspace_bytes = workspace_bytes or (workspace.numel() * workspace.element_size())
+    return o
+
+
+def lpa_detect(offsets, indices, weights, n, m, mode, k, tol, max_iter, labels_out,
+               stats: lpa_stats | None = None):
+    _check(load().lpa_detect(_ptr(offsets), _ptr(indices), _ptr(weights), n, m, _mode(mode),
+                             k, tol, max_iter, _ptr(labels_out),
+                             ctypes.byref(stats) if stats is not None else None))
+
+
+def lpa_detect_ex(offsets, indices, weights, n, m, mode, k, tol, max_iter, labels_out,
+                  stats: lpa_stats | None = None, opt: lpa_options | None = None):
+    _check(load().lpa_detect_ex(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                _mode(mode), k, tol, max_iter, _ptr(labels_out),
+                                ctypes.byref(stats) if stats is not None else None,
+                                ctypes.byref(opt) if opt is not None else None))
+
+
+def lpa_detect_host(offsets, indices, weights, n, m, mode, k, tol, max_iter, labels_out,
+                    stats: lpa_stats | None = None, opt: lpa_options | None = None):
+    _check(load().lpa_detect_host(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                  _mode(mode), k, tol, max_iter, _ptr(labels_out),
+                                  ctypes.byref(stats) if stats is not None else None,
+                                  ctypes.byref(opt) if opt is not None else None))
+
+
+def lpa_modularity(offsets, indices, weights, n, m, labels) -> float:
+    q = ctypes.c_double()
+    _check(load().lpa_modularity(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                 _ptr(labels), ctypes.byref(q)))
+    return float(q.value)
+
+
+def lpa_modularity_ex(offsets, indices, weights, n, m, labels,
+                      opt: lpa_options | None = None) -> float:
+    q = ctypes.c_double()
+    _check(load().lpa_modularity_ex(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                    _ptr(labels), ctypes.byref(q),
+                                    ctypes.byref(opt) if opt is not None else None))
+    return float(q.value)
+
+
+def lpa_workspace_size(n, m, mode, k=8) -> int:
+    return int(load().lpa_workspace_size(n, m, _mode(mode), k))
+
+
+def lpa_modularity_workspace_size(n) -> int:
+    return int(load().lpa_modularity_workspace_size(n))
+
+
+def lpa_plan_create(offsets, indices, weights, n, m, mode, k, opt: lpa_options | None = None):
+    h = ctypes.c_void_p()
+    _check(load().lpa_plan_create(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                  _mode(mode), k,
+                                  ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.byref(h)))
+    return h.value
+
+
+def lpa_plan_sweep(plan, c_prev, c_next, pick_less, want_dn=True):
+    dn = ctypes.c_int64()
+    _check(load().lpa_plan_sweep(plan, _ptr(c_prev), _ptr(c_next), int(bool(pick_less)),
+                                 ctypes.byref(dn) if want_dn else None))
+    return int(dn.value) if want_dn else None
+
+
+def lpa_plan_run(plan, tol, max_iter, labels_out, stats: lpa_stats | None = None):
+    _check(load().lpa_plan_run(plan, tol, max_iter, _ptr(labels_out),
+                               ctypes.byref(stats) if stats is not None else None))
+
+
+def lpa_plan_destroy(plan):
+    _check(load().lpa_plan_destroy(plan))
+
+
+def lpa_version() -> str:
+    return load().lpa_version().decode()
+
+
+# ----------------------------------------------------------- tensor conveniences
+
+
+class Plan:
+    """A binned graph on the device (``lpa_plan_*``); use as a context manager."""
+
+    def __init__(self, offsets, indices, weights=None, mode="mg", k=8, **opts):
+        self.n = int(offsets.numel() - 1)
+        self.m = int(indices.numel())
+        self._keep = (offsets, indices, weights, opts.get("labels_in"))
+        self.opt = make_options(**opts)
+        self.handle = lpa_plan_create(offsets, indices, weights, self.n, self.m, mode, k,
+                                      self.opt)
+
+    def sweep(self, c_prev, c_next, pick_less=False, want_dn=True):
+        return lpa_plan_sweep(self.handle, c_prev, c_next, pick_less, want_dn)
+
+    def run(self, labels_out, tol=0.05, max_iter=20) -> dict:
+        st = lpa_stats()
+        lpa_plan_run(self.handle, tol, max_iter, labels_out, st)
+        return st.to_dict()
+
+    def close(self):
+        if self.handle:
+            lpa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def detect(offsets, indices, weights=None, mode="mg", k=8, tol=0.05, max_iter=20,
+           labels_out=None, **opts):
+    """Run LPA on device tensors; returns (labels tensor, stats dict)."""
+    import torch
+
+    n = int(offsets.numel() - 1)
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    st = lpa_stats()
+    lpa_detect_ex(offsets, indices, weights, n, int(indices.numel()), mode, k, tol, max_iter,
+                  labels_out, st, make_options(**opts))
+    return labels_out, st.to_dict()
+
+
+def modularity(offsets, indices, weights, labels, **opts) -> float:
+    """Modularity (Eq. 1) of device labels."""
+    n = int(offsets.numel() - 1)
+    return lpa_modularity_ex(offsets, indices, weights, n, int(indices.numel()), labels,
+                             make_options(**opts))

@@ -483,43 +483,37 @@ int gg_lfr(int64_t n, double gamma_d, int32_t dmin, int32_t dmax, double gamma_c
     for (int64_t i = 0; i < n; ++i) vorder[h[maxk - kin[i]]++] = (int32_t)i;
     free(h);
   }
-  /* placement: community of each (original) vertex */
+  /* placement: community of each (original) vertex.  Vertices come in descending
+   * internal degree, so the set of communities large enough only grows; `open` holds
+   * those with room, and a vertex picks one uniformly.  If none is left, it takes the
+   * largest smaller community with room and its internal degree is capped. */
   int32_t* comm = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   int64_t* room = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
+  int64_t* open = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
   for (int64_t c = 0; c < nc; ++c) room[c] = csize[c];
   rng_t rp = rng_stream(seed, 303, 0);
-  int64_t full_prefix = 0; /* corder[0 .. full_prefix) are known full (smallest first) */
+  int64_t nopen = 0, hi = nc, fb = nc - 1;
   for (int64_t t = 0; t < n; ++t) {
     int32_t v = vorder[t];
-    /* first position in corder whose size exceeds kin[v] */
-    int64_t lo = 0, hi = nc;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) / 2;
-      if (csize[corder[mid]] > kin[v]) hi = mid; else lo = mid + 1;
+    while (hi > 0 && csize[corder[hi - 1]] > kin[v]) {
+      --hi;
+      if (room[corder[hi]] > 0) open[nopen++] = corder[hi];
     }
-    int64_t chosen = -1;
-    if (lo < nc) {
-      for (int tries = 0; tries < 32 && chosen < 0; ++tries) {
-        int64_t c = corder[lo + (int64_t)rng_below(&rp, (uint64_t)(nc - lo))];
-        if (room[c] > 0) chosen = c;
-      }
-      if (chosen < 0) {
-        int64_t s0 = lo + (int64_t)rng_below(&rp, (uint64_t)(nc - lo));
-        for (int64_t q = 0; q < nc - lo && chosen < 0; ++q) {
-          int64_t c = corder[lo + (s0 - lo + q) % (nc - lo)];
-          if (room[c] > 0) chosen = c;
-        }
-      }
-    }
-    if (chosen < 0) {
-      while (full_prefix < nc && room[corder[full_prefix]] == 0) ++full_prefix;
-      for (int64_t q = full_prefix; q < nc && chosen < 0; ++q)
-        if (room[corder[q]] > 0) chosen = corder[q];
+    int64_t chosen;
+    if (nopen > 0) {
+      int64_t q = (int64_t)rng_below(&rp, (uint64_t)nopen);
+      chosen = open[q];
+      if (room[chosen] == 1) open[q] = open[--nopen];
+    } else {
+      if (fb > hi - 1) fb = hi - 1;
+      while (fb >= 0 && room[corder[fb]] == 0) --fb;
+      chosen = corder[fb]; /* total room equals the vertices left, so one exists */
       if (kin[v] > csize[chosen] - 1) kin[v] = (int32_t)(csize[chosen] - 1);
     }
     room[chosen]--;
     comm[v] = (int32_t)chosen;
   }
+  free(open);
   free(room);
   free(vorder);
   free(corder);
@@ -571,19 +565,21 @@ int gg_lfr(int64_t n, double gamma_d, int32_t dmin, int32_t dmax, double gamma_c
     for (int64_t i = 0; i < n; ++i) comm_out[newid[i]] = comm[i];
   }
   /* stubs: internal ones grouped by community (in member order), external ones global */
+  /* community c's internal stubs occupy [ioff[c], ioff[c] + ilen[c]), in id order */
   int64_t* ioff = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nc + 1));
-  int64_t next = 0;
+  int64_t* ilen = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nc + 1));
+  int64_t next = 0, nin = 0;
   {
-    int64_t acc = 0;
     for (int64_t q = 0; q < nc; ++q) {
       int64_t c = cperm[q];
-      ioff[c] = acc;
-      for (int64_t p = cstart[c]; p < cstart[c] + csize[c]; ++p) acc += kin[members[p]];
+      ioff[c] = nin;
+      int64_t len = 0;
+      for (int64_t p = cstart[c]; p < cstart[c] + csize[c]; ++p) len += kin[members[p]];
+      ilen[c] = len;
+      nin += len;
     }
-    ioff[nc] = acc;
     for (int64_t i = 0; i < n; ++i) next += deg[i] - kin[i];
   }
-  int64_t nin = ioff[nc];
   int32_t* istub = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nin > 0 ? nin : 1));
   int32_t* estub = (int32_t*)malloc(sizeof(int32_t) * (size_t)(next > 0 ? next : 1));
 #pragma omp parallel for num_threads(T) schedule(dynamic, 64)
@@ -602,23 +598,24 @@ int gg_lfr(int64_t n, double gamma_d, int32_t dmin, int32_t dmax, double gamma_c
     }
   }
   free(members);
+  free(newid);
   free(deg);
   free(kin);
   free(comm);
   /* pair stubs at random */
 #pragma omp parallel for num_threads(T) schedule(dynamic, 1)
   for (int64_t c = 0; c < nc; ++c) {
-    int64_t len = ioff[c + 1] - ioff[c];
+    int64_t len = ilen[c];
     if (len >= (1 << 22)) continue; /* large ones below, in parallel */
     shuffle_i32(istub + ioff[c], len, seed ^ mix64((uint64_t)c), 307, 1);
   }
   for (int64_t c = 0; c < nc; ++c) {
-    int64_t len = ioff[c + 1] - ioff[c];
+    int64_t len = ilen[c];
     if (len >= (1 << 22)) shuffle_i32(istub + ioff[c], len, seed ^ mix64((uint64_t)c), 307, T);
   }
   shuffle_i32(estub, next, seed, 309, T);
   int64_t npairs = 0;
-  for (int64_t c = 0; c < nc; ++c) npairs += (ioff[c + 1] - ioff[c]) / 2;
+  for (int64_t c = 0; c < nc; ++c) npairs += ilen[c] / 2;
   npairs += next / 2;
   int32_t* u = (int32_t*)malloc(sizeof(int32_t) * (size_t)(npairs > 0 ? npairs : 1));
   int32_t* v = (int32_t*)malloc(sizeof(int32_t) * (size_t)(npairs > 0 ? npairs : 1));
@@ -626,7 +623,7 @@ int gg_lfr(int64_t n, double gamma_d, int32_t dmin, int32_t dmax, double gamma_c
   {
     int64_t o = 0;
     for (int64_t c = 0; c < nc; ++c) {
-      int64_t len = ioff[c + 1] - ioff[c];
+      int64_t len = ilen[c];
       for (int64_t t = 0; t + 1 < len; t += 2) {
         u[o] = istub[ioff[c] + t];
         v[o] = istub[ioff[c] + t + 1];
@@ -642,6 +639,7 @@ int gg_lfr(int64_t n, double gamma_d, int32_t dmin, int32_t dmax, double gamma_c
   free(istub);
   free(estub);
   free(ioff);
+  free(ilen);
   free(cstart);
   free(cperm);
   free(csize);
