@@ -1,0 +1,442 @@
+"""Benchmark: MG8 label propagation on a GB300, one JSON line on stdout.
+
+A step is one whole run of the hot path on one synthetic graph resident in HBM: degree
+binning, synchronous sweeps to convergence (at most 20, pick-less every 8, tol 0.05) and
+the modularity of the result -- one ``lpa_detect_ex`` call.  ``value`` is edges processed
+per second (sum over steps of iterations * m, divided by the CUDA-event time of the
+timed steps).  ``e2e`` is the same metric through ``lpa_detect_host`` with the graph in
+page-locked host memory (host-to-device copy of the CSR and device-to-host copy of the
+labels inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload lfr26|rmat22|pp1000] [--mode mg|bm|exact]
+
+Under torchrun (N > 1) every rank solves its own replica (the single-graph path does not
+shard; scaling is weak) and rank 0 prints the line with the max time over ranks.
+``--impl reference`` times the CPU oracle (the only reference this method has) on the
+host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "MG8-LPA edges/sec/iteration"
+UNIT = "edges/s"
+
+# DRAM traffic of one sweep launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the workload named below, scaled per launch, and the hash of
+# the sweep kernel source it was taken with.  If the source changes, traffic is reported
+# as null until a new capture is taken.
+SWEEP_TRAFFIC = {"src_sha256": None, "workload": None, "bytes_per_launch": None}
+
+WORKLOADS = {
+    "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
+             "[4, 65536], community sizes power law 1.5 on [20, 1e6], mu=0.2, integer "
+             "weights 1..8, community-contiguous ids, seed 0",
+    "lfr22": "LFR-style heavy-tailed planted partition as lfr26 but n=2^22 (profiling size)",
+    "rmat22": "R-MAT scale 22, edge factor 16, (a,b,c)=(0.57,0.19,0.19), symmetrised, "
+              "duplicates merged with summed weights, seed 0",
+    "pp1000": "planted partition, 1000 vertices in 10 communities, p_in=0.1, p_out=0.005, "
+              "unit weights, seed 0",
+}
+
+
+def make_graph(name: str) -> synth.Graph:
+    if name == "lfr26":
+        return synth.lfr(n=2**26, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
+                         cmax=10**6, mu=0.2, wmax=8, seed=0)
+    if name == "lfr22":
+        return synth.lfr(n=2**22, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
+                         cmax=10**6, mu=0.2, wmax=8, seed=0)
+    if name == "rmat22":
+        return synth.rmat(scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=0)
+    if name == "pp1000":
+        return synth.planted_partition(n=1000, ncomm=10, p_in=0.1, p_out=0.005, seed=0)
+    raise ValueError(name)
+
+
+def sweep_src_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("lpa_sweep.cu", "lpa_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2411_19901_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def mark(self, which: str):
+        """Host time at the start / end of the timed region."""
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = getattr(self, "start", None), getattr(self, "end", None)
+        parsed = []
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + r[0].split(".")[1]) if "." in r[0] else 0.0
+                parsed.append((ts, float(r[2]), float(r[3]), float(r[4]), r[6:10]))
+            except (ValueError, IndexError):
+                continue
+        inside = [p for p in parsed if t0 is not None and t0 - 0.2 <= p[0] <= t1 + 0.2]
+        for ts, a, b, c, flags in (inside or parsed):
+            sm.append(a)
+            smax.append(b)
+            power.append(c)
+            for name, val in zip(names, flags):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None,
+            "samples": len(sm),
+            "samples_in_timed_region": len(inside),
+            "reasons": sorted(reasons),
+        }
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def physical_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts) and parts[local_rank].strip().isdigit():
+            return int(parts[local_rank])
+    return local_rank
+
+
+def share_graph(name: str, world: int, rank: int, barrier) -> tuple[synth.Graph, float]:
+    """Rank 0 generates; with several ranks the others map rank 0's arrays from disk."""
+    t0 = time.perf_counter()
+    if world == 1:
+        g = make_graph(name)
+        return g, time.perf_counter() - t0
+    d = os.path.join(tempfile.gettempdir(), f"lpa_bench_{name}")
+    if rank == 0:
+        g = make_graph(name)
+        os.makedirs(d, exist_ok=True)
+        np.save(os.path.join(d, "offsets.npy"), g.offsets)
+        np.save(os.path.join(d, "indices.npy"), g.indices)
+        if g.weights is not None:
+            np.save(os.path.join(d, "weights.npy"), g.weights)
+    barrier()
+    if rank != 0:
+        off = np.load(os.path.join(d, "offsets.npy"), mmap_mode="r")
+        idx = np.load(os.path.join(d, "indices.npy"), mmap_mode="r")
+        wp = os.path.join(d, "weights.npy")
+        w = np.load(wp, mmap_mode="r") if os.path.exists(wp) else None
+        g = synth.Graph(off, idx, w, name)
+    return g, time.perf_counter() - t0
+
+
+def sweep_bytes(n: int, m: int, weighted: bool) -> int:
+    """Algorithmic bytes of one sweep: per CSR entry its index, weight and the gathered
+    neighbour label; per vertex its offset, old label and new label."""
+    return (12 if weighted else 8) * m + 16 * n
+
+
+def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int):
+    """Time full oracle sweeps (iteration 0 from identity labels) on all host cores."""
+    import oracle
+
+    om = {"mg": oracle.MG, "bm": oracle.BM, "exact": oracle.EXACT}[mode]
+    threads = os.cpu_count() or 1
+    offs = np.ascontiguousarray(g.offsets)
+    idx = np.ascontiguousarray(g.indices)
+    w = None if g.weights is None else np.ascontiguousarray(g.weights)
+    c0 = np.arange(g.n, dtype=np.int32)
+    times = []
+    while len(times) < max_reps and sum(times) < seconds:
+        t = time.perf_counter()
+        oracle.move(offs, idx, w, c0, mode=om, k=8, pick_less=True, threads=threads)
+        times.append(time.perf_counter() - t)
+    return times, threads
+
+
+# ------------------------------------------------------------------ arms
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    g = make_graph(args.workload)
+    import oracle  # noqa: F401  (the reference arm is the CPU oracle)
+
+    om_times, threads = [], 0
+    for step in range(args.warmup + args.steps):
+        ts, threads = oracle_sweeps(g, args.mode, 0.0, 1)
+        if step >= args.warmup:
+            om_times += ts
+    value = len(om_times) * g.m / sum(om_times)
+    sample = f"{len(om_times)} full oracle sweeps (iteration 0 from identity labels) of the graph"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(om_times) / len(om_times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(args, g),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, g):
+    return {
+        "workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+        "n": g.n, "m": g.m, "mode": args.mode, "k": 8, "tol": 0.05, "max_iter": 20,
+        "pl_period": 8, "weights": "int-valued fp32" if g.weights is not None else "unit",
+        "l2": "inputs larger than L2 (no flush)" if g.m * 8 > 129e6 else
+              "inputs smaller than L2 (warm cache)",
+        "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+    }
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2411_19901_gb300 as lpa
+    from paper_2411_19901_gb300 import build
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+    dev = torch.device("cuda", local)
+    build.build()
+    g, gen_s = share_graph(args.workload, world, rank, barrier)
+    n, m = g.n, g.m
+    weighted = g.weights is not None
+
+    # page-locked host copies (the e2e inputs) and device copies (the value inputs)
+    pin = world == 1
+    h_off = torch.from_numpy(np.ascontiguousarray(g.offsets))
+    h_idx = torch.from_numpy(np.ascontiguousarray(g.indices))
+    h_w = torch.from_numpy(np.ascontiguousarray(g.weights)) if weighted else None
+    if pin:
+        h_off, h_idx = h_off.pin_memory(), h_idx.pin_memory()
+        h_w = h_w.pin_memory() if weighted else None
+    d_off = h_off.to(dev)
+    d_idx = h_idx.to(dev)
+    d_w = h_w.to(dev) if weighted else None
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(lpa.lpa_workspace_size(n, m, args.mode), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opt = lpa.make_options(validate=False, timing=True, modularity=True, stream=stream,
+                           workspace=ws)
+
+    def step():
+        st = lpa.lpa_stats()
+        lpa.lpa_detect_ex(d_off, d_idx, d_w, n, m, args.mode, 8, 0.05, 20, labels, st, opt)
+        return st.to_dict()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = ClockSampler(physical_gpu_index(local))
+    launches0 = lpa.lpa_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    time.sleep(0.5)  # let nvidia-smi start sampling
+    torch.cuda.synchronize(dev)
+    clocks.mark("start")
+    ev0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark("end")
+    barrier()
+    clk = clocks.stop()
+    launches = lpa.lpa_launch_count() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    edges = sum(s["iterations"] * m for s in stats)
+    sweeps = sum(s["iterations"] for s in stats)
+    sweep_ms = sum(s["sweep_ms"] for s in stats)
+
+    # end to end through the host-memory entry point
+    e2e_steps = max(1, min(args.steps, 3))
+    h_lab = torch.empty(n, dtype=torch.int32, pin_memory=pin)
+    e2e_stats = []
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_host = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        st = lpa.lpa_stats()
+        lpa.lpa_detect_host(h_off.numpy(), h_idx.numpy(), h_w.numpy() if weighted else None,
+                            n, m, args.mode, 8, 0.05, 20, h_lab.numpy(), st,
+                            lpa.make_options(validate=False, modularity=True, stream=stream,
+                                             workspace=ws))
+        e2e_stats.append(st.to_dict())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
+    barrier()
+    e2e_edges = sum(s["iterations"] * m for s in e2e_stats)
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, e2e_ms = float(t[0]), float(t[1])
+        tot = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        edges_all, e2e_edges_all = float(tot[0]), float(tot[1])
+    else:
+        edges_all, e2e_edges_all = float(edges), float(e2e_edges)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_hbm_peak()
+    launch_ms = sweep_ms / max(sweeps, 1)
+    alg_bytes = sweep_bytes(n, m, weighted)
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = None
+    if SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha() and SWEEP_TRAFFIC["workload"] == args.workload:
+        traffic = SWEEP_TRAFFIC["bytes_per_launch"]
+    cpu = None
+    if world == 1:
+        times, threads = oracle_sweeps(g, args.mode, seconds=10.0, max_reps=3)
+        cpu = {"value": len(times) * m / sum(times), "unit": UNIT, "cores": threads,
+               "kind": "oracle",
+               "sample": f"{len(times)} full oracle sweep(s) (iteration 0 from identity "
+                         f"labels) of the same graph, {sum(times):.1f} s"}
+    h2d = 8 * (n + 1) + 4 * m + (4 * m if weighted else 0)
+    d2h = 4 * n + 64 + 32 + 64 + 8 * 20
+    line = {
+        "metric": METRIC, "value": edges_all / (elapsed_ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(args, g),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "sweep_sketch_kernel<MGSketch<8>>",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_edges_all / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pinned_host_memory": pin},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "iterations": [s["iterations"] for s in stats],
+        "modularity": stats[-1]["modularity"],
+        "setup_ms": stats[-1]["setup_ms"],
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lfr26")
+    ap.add_argument("--mode", choices=["mg", "bm", "exact"], default="mg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: the timing rules want at least 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

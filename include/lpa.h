@@ -55,6 +55,7 @@ typedef enum {
 /* Flags for lpa_options.flags. */
 #define LPA_VALIDATE 0x1u /* check the CSR (and labels_in) on the device first */
 #define LPA_TIMING 0x2u   /* time the sweep and binning kernels with CUDA events */
+#define LPA_MODULARITY 0x4u /* also compute the modularity of the result (Eq. 1) */
 
 /* Largest max_iter accepted; lpa_stats.changed has this many entries. */
 #define LPA_MAX_ITER 1024
@@ -72,6 +73,7 @@ typedef struct {
   size_t device_bytes;              /* device workspace bytes used */
   int32_t chunks;                   /* CTA work units of the binned graph */
   int32_t hubs;                     /* vertices swept by a whole CTA */
+  double modularity;                /* Q of the result (LPA_MODULARITY), else 0 */
 } lpa_stats;
 
 /* Options.  Call lpa_options_init first; it sets the paper's defaults (Sec. 5.1.2). */
@@ -83,7 +85,8 @@ typedef struct {
                                Default 64. */
   int32_t leaf_max;         /* Lmax: most partial sketches per row, power of two
                                <= 256.  Default 256. */
-  uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING.  Default LPA_VALIDATE. */
+  uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY.
+                               Default LPA_VALIDATE. */
   const int32_t* labels_in; /* device, n labels in [0, n) to start from; NULL = C[i]=i */
   void* stream;             /* cudaStream_t; NULL = legacy default stream */
   void* workspace;          /* device scratch of workspace_bytes bytes, 256-byte
@@ -173,6 +176,8 @@ const char* lpa_status_string(lpa_status s);
 const char* lpa_last_error(void);
 /* Library version string. */
 const char* lpa_version(void);
+/* Number of CUDA kernels this library has launched in this process (diagnostics). */
+uint64_t lpa_launch_count(void);
 
 #ifdef __cplusplus
 }

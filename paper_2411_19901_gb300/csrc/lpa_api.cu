@@ -17,6 +17,8 @@
 
 using namespace lpa;
 
+std::atomic<unsigned long long> lpa::g_launches{0};
+
 namespace {
 
 thread_local std::string g_err;
@@ -44,7 +46,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of a plan; offsets in bytes from the workspace base.
 struct Layout {
-  size_t state, dn, tmp, cv0, cv1, hubs, hub_tab, seg, tab_keys, tab_vals, total_fixed, total;
+  size_t state, dn, tmp, cv0, cv1, hubs, hub_tab, seg, sigma, partials, out4, tab_keys,
+      tab_vals, total_fixed, total;
 };
 
 Layout layout(int64_t n, int64_t m, int mode, int64_t tab_slots) {
@@ -66,6 +69,12 @@ Layout layout(int64_t n, int64_t m, int mode, int64_t tab_slots) {
   o = align256(o + (mode == kExact ? sizeof(int64_t) * (size_t)(n + 1) : 0));
   L.seg = o;
   o = align256(o + 3 * sizeof(int64_t) * (size_t)(num_segments(n) + 1));
+  L.sigma = o;  // modularity: Sigma_c per label, per-block partials, results
+  o = align256(o + sizeof(double) * (size_t)n);
+  L.partials = o;
+  o = align256(o + sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
+  L.out4 = o;
+  o = align256(o + sizeof(double) * 4);
   L.total_fixed = o;
   L.tab_keys = o;
   o = align256(o + sizeof(int32_t) * (size_t)tab_slots);
@@ -109,6 +118,7 @@ struct lpa_plan_s {
   std::vector<cudaEvent_t> events;  // timing pairs, created on demand
   DevState* host_state = nullptr;   // page-locked mirrors
   unsigned long long* host_dn = nullptr;
+  double* host_q = nullptr;
 };
 
 namespace {
@@ -162,6 +172,7 @@ void destroy_plan(lpa_plan_s* p) {
   if (p->own_ws || p->own_tab) cudaStreamSynchronize(p->stream);
   if (p->host_state) cudaFreeHost(p->host_state);
   if (p->host_dn) cudaFreeHost(p->host_dn);
+  if (p->host_q) cudaFreeHost(p->host_q);
   delete p;
 }
 
@@ -205,6 +216,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   };
   cudaError_t ce = cudaMallocHost((void**)&p->host_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_dn, sizeof(unsigned long long) * LPA_MAX_ITER);
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_q, sizeof(double) * 4);
   if (ce != cudaSuccess)
     return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
 
@@ -354,6 +366,13 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
     LPA_CUDA(launch_converge(p->st, p->dn, l, pick_less, tol, n, s));
   }
   LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
+  const bool want_q = (p->flags & LPA_MODULARITY) != 0;
+  if (want_q) {
+    double* out4 = (double*)(p->ws + p->lay.out4);
+    LPA_CUDA(launch_modularity(p->off, p->idx, p->w, labels_out, n, (double*)(p->ws + p->lay.sigma),
+                               (double*)(p->ws + p->lay.partials), modularity_partials(n), out4, s));
+    LPA_CUDA(cudaMemcpyAsync(p->host_q, out4, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  }
   LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   if (max_iter > 0)
     LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn, sizeof(unsigned long long) * max_iter,
@@ -372,6 +391,7 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
     stats->chunks = (int32_t)p->nchunks;
     stats->hubs = (int32_t)p->nhubs;
     stats->setup_ms = p->setup_ms;
+    stats->modularity = want_q ? p->host_q[3] : 0.0;
     if (timing) {
       double tot = 0.0;
       for (int l = 0; l < iters; ++l) {
@@ -594,5 +614,7 @@ const char* lpa_status_string(lpa_status s) {
 const char* lpa_last_error(void) { return g_err.c_str(); }
 
 const char* lpa_version(void) { return "lpa-gb300 0.1 (sm_103a)"; }
+
+uint64_t lpa_launch_count(void) { return (uint64_t)g_launches.load(); }
 
 }  // extern "C"

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace lpa {
 
 constexpr int kThreads = 256;          // threads per CTA; also max leaves per chunk
@@ -122,5 +124,9 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const floa
 int modularity_partials(int32_t n);
 
 inline int64_t num_segments(int64_t n) { return (n + kSegment - 1) / kSegment; }
+
+// Kernels launched by the library (counted at every launch site).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace lpa

@@ -313,9 +313,11 @@ inline unsigned grid_for(int64_t work, int threads, unsigned cap = 152 * 16) {
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int32_t n,
                             int64_t m, const int32_t* labels_in, int32_t* err, cudaStream_t s) {
   validate_offsets_kernel<<<grid_for((int64_t)n + 1, 256), 256, 0, s>>>(off, n, m, err);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   validate_edges_kernel<<<grid_for(m > n ? m : n, 256), 256, 0, s>>>(idx, w, n, m, labels_in, err);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -325,24 +327,29 @@ cudaError_t launch_bin(const BinArgs& b, DevState* st, cudaStream_t s, bool writ
   const unsigned grid = (unsigned)((nseg + 127) / 128);
   if (!write_pass) {
     bin_count_kernel<<<grid, 128, 0, s>>>(b, nseg);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     scan3_kernel<<<1, kScanThreads, 0, s>>>(b.seg_chunks, b.seg_hubs, b.seg_hub_edges, nseg, st);
+    count_launch();
     return cudaGetLastError();
   }
   bin_write_kernel<<<grid, 128, 0, s>>>(b, nseg);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   init_labels_kernel<<<grid_for(n, 256), 256, 0, s>>>(c, labels_in, n);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_converge(DevState* st, const unsigned long long* dn, int l, int pick_less,
                             double tol, int32_t n, cudaStream_t s) {
   converge_kernel<<<1, 32, 0, s>>>(st, dn, l, pick_less, tol, n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -350,12 +357,14 @@ cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp
                             cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(st, out, tmp, n);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   fill_i32_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -363,6 +372,7 @@ cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long value, int
                             cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   fill_u64_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -375,18 +385,23 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const floa
                               const int32_t* labels, int32_t n, double* sigma_c, double* partials,
                               int32_t npart, double* out3, cudaStream_t s) {
   fill_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(sigma_c, n);
+  count_launch();
   fill_f64_kernel<<<grid_for(3 * (int64_t)npart, 256), 256, 0, s>>>(partials, 3 * (int64_t)npart);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (n > 0) {
     modularity_rows_kernel<<<npart, kModThreads, 0, s>>>(off, idx, w, labels, n, sigma_c, partials);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     modularity_sq_kernel<<<npart, kModThreads, 0, s>>>(sigma_c, n, partials);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   modularity_final_kernel<<<1, 32, 0, s>>>(partials, npart, out3);
+  count_launch();
   return cudaGetLastError();
 }
 

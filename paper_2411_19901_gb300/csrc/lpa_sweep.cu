@@ -544,6 +544,7 @@ cudaError_t launch_sketch(const SweepArgs& a, size_t smem, cudaStream_t s) {
   const unsigned grid = (unsigned)(a.nhubs + a.nchunks);
   if (grid == 0) return cudaSuccess;
   kern<<<grid, kThreads, smem, s>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -573,6 +574,7 @@ cudaError_t launch_sweep(int mode, int k, bool weighted, const SweepArgs& a, cud
     const unsigned grid = (unsigned)(a.nhubs + a.nchunks);
     if (grid == 0) return cudaSuccess;
     kern<<<grid, kThreads, smem, s>>>(a);
+    count_launch();
     return cudaGetLastError();
   }
   switch (k) {

@@ -20,6 +20,7 @@ LPA_EXACT, LPA_MG, LPA_BM = 0, 1, 2
 MODES = {"exact": LPA_EXACT, "mg": LPA_MG, "bm": LPA_BM}
 LPA_VALIDATE = 0x1
 LPA_TIMING = 0x2
+LPA_MODULARITY = 0x4
 LPA_MAX_ITER = 1024
 
 STATUS = {0: "LPA_OK", -1: "LPA_EINVAL", -2: "LPA_ENOMEM", -3: "LPA_ECUDA",
@@ -45,6 +46,7 @@ class lpa_stats(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("chunks", ctypes.c_int32),
         ("hubs", ctypes.c_int32),
+        ("modularity", ctypes.c_double),
     ]
 
     def to_dict(self) -> dict:
@@ -61,6 +63,7 @@ class lpa_stats(ctypes.Structure):
             "device_bytes": int(self.device_bytes),
             "chunks": int(self.chunks),
             "hubs": int(self.hubs),
+            "modularity": float(self.modularity),
         }
 
 
@@ -104,6 +107,7 @@ _SIG = {
     "lpa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lpa_last_error": (ctypes.c_char_p, []),
     "lpa_version": (ctypes.c_char_p, []),
+    "lpa_launch_count": (ctypes.c_uint64, []),
 }
 
 EXPORTED = tuple(_SIG)
@@ -171,12 +175,14 @@ def lpa_options_init() -> lpa_options:
 
 
 def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=False,
-                 labels_in=None, stream=None, workspace=None, workspace_bytes=0) -> lpa_options:
+                 modularity=False, labels_in=None, stream=None, workspace=None,
+                 workspace_bytes=0) -> lpa_options:
     o = lpa_options_init()
     o.pl_period = pl_period
     o.leaf_e0 = leaf_e0
     o.leaf_max = leaf_max
-    o.flags = (LPA_VALIDATE if validate else 0) | (LPA_TIMING if timing else 0)
+    o.flags = ((LPA_VALIDATE if validate else 0) | (LPA_TIMING if timing else 0)
+               | (LPA_MODULARITY if modularity else 0))
     o.labels_in = _ptr(labels_in)
     o.stream = _stream_handle(stream)
     if workspace is not None:
@@ -259,6 +265,10 @@ def lpa_plan_destroy(plan):
 
 def lpa_version() -> str:
     return load().lpa_version().decode()
+
+
+def lpa_launch_count() -> int:
+    return int(load().lpa_launch_count())
 
 
 # ----------------------------------------------------------- tensor conveniences
