@@ -144,6 +144,26 @@ lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices,
                              const float* weights, int32_t n, int64_t m,
                              const int32_t* labels, double* q_out, const lpa_options* opt);
 
+/* Modularity for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is an interface convenience.  Some callers cannot, or must not,
+ * allocate at the moment they ask for a result -- a host program whose own caching
+ * allocator already holds nearly all device memory, or a latency-critical loop where
+ * cudaMalloc / cudaFree would stall the GPU.  This call allocates nothing: its scratch
+ * is a fixed device array inside the library (about 8 MB, held on every GPU that loads
+ * the library until the process exits), so n must be <= LPA_NOALLOC_MAX_N; larger n
+ * returns LPA_EINVAL.  Arguments and result are as for lpa_modularity_ex (opt may be
+ * NULL: legacy default stream, LPA_VALIDATE on; workspace fields are ignored).
+ * The first call on each device looks up the array's device address once (with that
+ * device current); make that first call before any CUDA stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race and give wrong results, so order them.  Each call clears what it needs,
+ * so results never depend on an earlier call. */
+#define LPA_NOALLOC_MAX_N (1 << 20)
+lpa_status lpa_modularity_noalloc(const int64_t* offsets, const int32_t* indices,
+                                  const float* weights, int32_t n, int64_t m,
+                                  const int32_t* labels, double* q_out,
+                                  const lpa_options* opt);
+
 /* Device workspace an lpa_detect_ex call needs (an upper bound for any graph with these
  * sizes); lpa_modularity_ex needs lpa_modularity_workspace_size(n). */
 size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k);

@@ -85,6 +85,15 @@ Layout layout(int64_t n, int64_t m, int mode, int64_t tab_slots) {
   return L;
 }
 
+}  // namespace
+
+int lpa::set_last_error(int s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+
+namespace {
+
 bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
 
 }  // namespace

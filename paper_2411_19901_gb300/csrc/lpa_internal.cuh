@@ -125,6 +125,9 @@ int modularity_partials(int32_t n);
 
 inline int64_t num_segments(int64_t n) { return (n + kSegment - 1) / kSegment; }
 
+// Record the message returned by lpa_last_error() on this host thread; returns s.
+int set_last_error(int s, const char* msg);
+
 // Kernels launched by the library (counted at every launch site).
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

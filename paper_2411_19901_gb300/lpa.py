@@ -108,6 +108,8 @@ _SIG = {
     "lpa_last_error": (ctypes.c_char_p, []),
     "lpa_version": (ctypes.c_char_p, []),
     "lpa_launch_count": (ctypes.c_uint64, []),
+    "lpa_modularity_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P,
+                                              _P, _P]),
 }
 
 EXPORTED = tuple(_SIG)
@@ -227,6 +229,20 @@ def lpa_modularity_ex(offsets, indices, weights, n, m, labels,
     _check(load().lpa_modularity_ex(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
                                     _ptr(labels), ctypes.byref(q),
                                     ctypes.byref(opt) if opt is not None else None))
+    return float(q.value)
+
+
+LPA_NOALLOC_MAX_N = 1 << 20
+
+
+def lpa_modularity_noalloc(offsets, indices, weights, n, m, labels,
+                           opt: lpa_options | None = None) -> float:
+    """Modularity computed in the library's fixed device scratch (no device allocation;
+    n <= LPA_NOALLOC_MAX_N; concurrent calls race, see include/lpa.h)."""
+    q = ctypes.c_double()
+    _check(load().lpa_modularity_noalloc(_ptr(offsets), _ptr(indices), _ptr(weights), n, m,
+                                         _ptr(labels), ctypes.byref(q),
+                                         ctypes.byref(opt) if opt is not None else None))
     return float(q.value)
 
 
