@@ -72,7 +72,7 @@ def make_graph(name: str) -> synth.Graph:
 
 def sweep_src_sha() -> str:
     h = hashlib.sha256()
-    for f in ("lpa_sweep.cu", "lpa_internal.cuh"):
+    for f in ("lpa_sweep.cu", "lpa_sweep_impl.cuh", "lpa_fold.cuh", "lpa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2411_19901_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -400,7 +400,7 @@ def run_ours(args):
         "config": config_of(args, g),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "sweep_sketch_kernel<MGSketch<8>>",
+                     "kernel": "sweep_warp_kernel<MGSketch<8>, weighted>",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,

@@ -4,7 +4,8 @@
 // The driver never waits on the host between iterations: it enqueues max_iter
 // {sweep, convergence test} pairs; once the on-device test has fired, later sweeps exit
 // on their first instruction.  The host synchronises once, at the end, to read the
-// statistics.
+// statistics.  Sketch modes (MG, BM) run the warp-per-row sweep over a class binning;
+// the exact mode runs its chunk kernel over the chunk/hub binning.
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -44,46 +45,59 @@ lpa_status fail(lpa_status s, const char* fmt, ...) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+int64_t num_windows(int64_t n) { return (n + kWinVerts - 1) / kWinVerts; }
+
 // Workspace layout of a plan; offsets in bytes from the workspace base.
 struct Layout {
-  size_t state, dn, tmp, cv0, cv1, hubs, hub_tab, seg, sigma, partials, out4, tab_keys,
-      tab_vals, total_fixed, total;
+  size_t state, dn, dn_total, tmp;
+  // sketch modes
+  size_t perm_low, cnt_low, cls_list, counts, cursors;
+  // exact mode
+  size_t cv0, cv1, hubs, hub_tab, seg;
+  // modularity
+  size_t sigma, partials, out4;
+  size_t total_fixed, tab_keys, tab_vals, total;
 };
 
-Layout layout(int64_t n, int64_t m, int mode, int64_t tab_slots) {
+Layout layout(int64_t n, int mode, int64_t tab_slots) {
   Layout L{};
   size_t o = 0;
-  L.state = o;
-  o = align256(o + sizeof(DevState));
-  L.dn = o;
-  o = align256(o + sizeof(unsigned long long) * LPA_MAX_ITER);
-  L.tmp = o;
-  o = align256(o + sizeof(int32_t) * (size_t)n);
-  L.cv0 = o;
-  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
-  L.cv1 = o;
-  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
-  L.hubs = o;
-  o = align256(o + sizeof(int32_t) * (size_t)(n + 1));
-  L.hub_tab = o;
-  o = align256(o + (mode == kExact ? sizeof(int64_t) * (size_t)(n + 1) : 0));
-  L.seg = o;
-  o = align256(o + 3 * sizeof(int64_t) * (size_t)(num_segments(n) + 1));
-  L.sigma = o;  // modularity: Sigma_c per label, per-block partials, results
-  o = align256(o + sizeof(double) * (size_t)n);
-  L.partials = o;
-  o = align256(o + sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
-  L.out4 = o;
-  o = align256(o + sizeof(double) * 4);
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.state = take(sizeof(DevState));
+  L.dn = take(sizeof(unsigned long long) * LPA_MAX_ITER * kDnSlots);
+  L.dn_total = take(sizeof(unsigned long long) * LPA_MAX_ITER);
+  L.tmp = take(sizeof(int32_t) * (size_t)n);
+  if (mode == kExact) {
+    L.cv0 = take(sizeof(int32_t) * (size_t)(n + 1));
+    L.cv1 = take(sizeof(int32_t) * (size_t)(n + 1));
+    L.hubs = take(sizeof(int32_t) * (size_t)(n + 1));
+    L.hub_tab = take(sizeof(int64_t) * (size_t)(n + 1));
+    L.seg = take(3 * sizeof(int64_t) * (size_t)(num_segments(n) + 1));
+    L.partials = take(sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
+  } else {
+    const int64_t nwin = num_windows(n);
+    L.perm_low = take(sizeof(int32_t) * (size_t)(nwin * kWinVerts));
+    L.cnt_low = take(sizeof(int32_t) * (size_t)nwin);
+    L.cls_list = take(sizeof(int32_t) * (size_t)n);
+    L.counts = take(sizeof(unsigned long long) * 32);
+    L.cursors = take(sizeof(unsigned long long) * 32);
+    WarpPlan dummy{};
+    L.partials = take(sizeof(double) * (size_t)modularity_plan_partials(dummy, (int32_t)n));
+  }
+  L.sigma = take(sizeof(double) * (size_t)n);
+  L.out4 = take(sizeof(double) * 4);
   L.total_fixed = o;
-  L.tab_keys = o;
-  o = align256(o + sizeof(int32_t) * (size_t)tab_slots);
-  L.tab_vals = o;
-  o = align256(o + sizeof(float) * (size_t)tab_slots);
+  L.tab_keys = take(sizeof(int32_t) * (size_t)tab_slots);
+  L.tab_vals = take(sizeof(float) * (size_t)tab_slots);
   L.total = o;
-  (void)m;
   return L;
 }
+
+bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
 
 }  // namespace
 
@@ -91,12 +105,6 @@ int lpa::set_last_error(int s, const char* msg) {
   g_err = msg;
   return s;
 }
-
-namespace {
-
-bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
-
-}  // namespace
 
 struct lpa_plan_s {
   const int64_t* off = nullptr;
@@ -117,8 +125,10 @@ struct lpa_plan_s {
   Layout lay{};
   DevState* st = nullptr;
   unsigned long long* dn = nullptr;
+  unsigned long long* dn_total = nullptr;
   int32_t* tmp = nullptr;
-  int32_t *cv0 = nullptr, *cv1 = nullptr, *hubs = nullptr;
+  WarpPlan wp{};  // sketch modes
+  int32_t *cv0 = nullptr, *cv1 = nullptr, *hubs = nullptr;  // exact mode
   int64_t* hub_tab = nullptr;
   int32_t* tab_keys = nullptr;
   float* tab_vals = nullptr;
@@ -128,6 +138,7 @@ struct lpa_plan_s {
   DevState* host_state = nullptr;   // page-locked mirrors
   unsigned long long* host_dn = nullptr;
   double* host_q = nullptr;
+  unsigned long long* host_cls = nullptr;
 };
 
 namespace {
@@ -150,27 +161,34 @@ lpa_status ensure_events(lpa_plan_s* p, size_t count) {
   return LPA_OK;
 }
 
-lpa_status sweep_args(lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next, int pick_less,
-                      unsigned long long* dn, const int32_t* done, SweepArgs* a) {
-  a->off = p->off;
-  a->idx = p->idx;
-  a->w = p->w;
-  a->c_prev = c_prev;
-  a->c_next = c_next;
-  a->chunk_v0 = p->cv0;
-  a->chunk_v1 = p->cv1;
-  a->hubs = p->hubs;
-  a->hub_tab = p->hub_tab;
-  a->tab_keys = p->tab_keys;
-  a->tab_vals = p->tab_vals;
-  a->dn = dn;
-  a->done = done;
-  a->nchunks = (int32_t)p->nchunks;
-  a->nhubs = (int32_t)p->nhubs;
-  a->pick_less = pick_less;
-  a->e0 = p->e0;
-  a->lmax = p->lmax;
-  return LPA_OK;
+SweepArgs sweep_args(const lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next, int pick_less,
+                     unsigned long long* dn, const int32_t* done) {
+  SweepArgs a{};
+  a.off = p->off;
+  a.idx = p->idx;
+  a.w = p->w;
+  a.c_prev = c_prev;
+  a.c_next = c_next;
+  a.chunk_v0 = p->cv0;
+  a.chunk_v1 = p->cv1;
+  a.hubs = p->hubs;
+  a.hub_tab = p->hub_tab;
+  a.tab_keys = p->tab_keys;
+  a.tab_vals = p->tab_vals;
+  a.dn = dn;
+  a.done = done;
+  a.nchunks = (int32_t)p->nchunks;
+  a.nhubs = (int32_t)p->nhubs;
+  a.pick_less = pick_less;
+  a.e0 = p->e0;
+  a.lmax = p->lmax;
+  a.m = p->m;
+  return a;
+}
+
+cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
+  if (p->mode == kExact) return launch_sweep_exact(p->w != nullptr, a, p->stream);
+  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, a, p->wp, p->stream);
 }
 
 void destroy_plan(lpa_plan_s* p) {
@@ -182,7 +200,106 @@ void destroy_plan(lpa_plan_s* p) {
   if (p->host_state) cudaFreeHost(p->host_state);
   if (p->host_dn) cudaFreeHost(p->host_dn);
   if (p->host_q) cudaFreeHost(p->host_q);
+  if (p->host_cls) cudaFreeHost(p->host_cls);
   delete p;
+}
+
+// Class binning of the sketch modes: count classes, lay out the lists, fill them.
+lpa_status bin_classes(lpa_plan_s* p) {
+  cudaStream_t s = p->stream;
+  const int32_t n = p->n;
+  WarpPlan& wp = p->wp;
+  wp = WarpPlan{};
+  wp.perm_low = (const int32_t*)(p->ws + p->lay.perm_low);
+  wp.cnt_low = (const int32_t*)(p->ws + p->lay.cnt_low);
+  wp.cls_list = (const int32_t*)(p->ws + p->lay.cls_list);
+  wp.nwin = (int32_t)num_windows(n);
+  if (n == 0) return LPA_OK;
+  unsigned long long* counts = (unsigned long long*)(p->ws + p->lay.counts);
+  unsigned long long* cursors = (unsigned long long*)(p->ws + p->lay.cursors);
+  LPA_CUDA(launch_fill_u64(counts, 0ull, 32, s));
+  LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, counts, nullptr, nullptr, nullptr, nullptr,
+                           false, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 32,
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaStreamSynchronize(s));
+  int64_t acc = 0;
+  int64_t warps = 0;
+  for (int c = 0; c < kNumClasses; ++c) {
+    wp.cls_start[c] = acc;
+    acc += (int64_t)p->host_cls[c];
+  }
+  wp.cls_start[kNumClasses] = acc;
+  if (acc > n) return fail(LPA_EINTERNAL, "class binning counted %lld vertices", (long long)acc);
+  for (int c = 0; c < kMidClasses; ++c) {
+    wp.cls_warp_start[c] = (int32_t)warps;
+    const int L = 32 >> (c / kMidSub);
+    const int64_t cnt = (int64_t)p->host_cls[c];
+    warps += (cnt * L + 31) / 32;
+  }
+  wp.cls_warp_start[kMidClasses] = (int32_t)warps;
+  wp.nhubs = (int32_t)p->host_cls[kHubClass];
+  wp.mid_ctas = (int32_t)((warps + (kThreads / 32) - 1) / (kThreads / 32));
+  wp.low_ctas = (int32_t)((int64_t)wp.nwin * (kWinVerts / kThreads));
+  const int64_t grid = (int64_t)wp.nhubs + wp.mid_ctas + wp.low_ctas;
+  if (grid > 0x7fffffffLL) return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
+  for (int c = 0; c < kNumClasses; ++c) p->host_cls[c] = (unsigned long long)wp.cls_start[c];
+  LPA_CUDA(cudaMemcpyAsync(cursors, p->host_cls, sizeof(unsigned long long) * kNumClasses,
+                           cudaMemcpyHostToDevice, s));
+  LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, nullptr, (int32_t*)wp.perm_low,
+                           (int32_t*)wp.cnt_low, (int32_t*)wp.cls_list, cursors, true, s));
+  p->nhubs = wp.nhubs;
+  p->nchunks = (int64_t)wp.mid_ctas + wp.low_ctas;
+  return LPA_OK;
+}
+
+// Chunk binning of the exact mode.
+lpa_status bin_chunks(lpa_plan_s* p, const lpa_options& o) {
+  cudaStream_t s = p->stream;
+  const int32_t n = p->n;
+  const int64_t nseg = num_segments(n);
+  int64_t* seg = (int64_t*)(p->ws + p->lay.seg);
+  BinArgs b{};
+  b.off = p->off;
+  b.n = n;
+  b.cap = kChunkCapExact;
+  b.cost_floor = b.cap / kThreads;
+  b.e0 = p->e0;
+  b.lmax = p->lmax;
+  b.leaves = 0;
+  b.seg_chunks = seg;
+  b.seg_hubs = seg + (nseg + 1);
+  b.seg_hub_edges = seg + 2 * (nseg + 1);
+  b.chunk_v0 = p->cv0;
+  b.chunk_v1 = p->cv1;
+  b.hubs = p->hubs;
+  b.hub_tab = p->hub_tab;
+  if (n > 0) {
+    LPA_CUDA(launch_bin(b, p->st, s, false));
+    LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LPA_CUDA(cudaStreamSynchronize(s));
+    p->nchunks = p->host_state->nchunks;
+    p->nhubs = p->host_state->nhubs;
+    p->hub_edges = p->host_state->hub_edges;
+    if (p->nchunks + p->nhubs > 0x7fffffffLL || p->nchunks > n || p->nhubs > n)
+      return fail(LPA_EINTERNAL, "binning produced %lld chunks and %lld hubs",
+                  (long long)p->nchunks, (long long)p->nhubs);
+    LPA_CUDA(launch_bin(b, p->st, s, true));
+  }
+  if (p->hub_edges > 0) {
+    const int64_t slots = 2 * p->hub_edges;
+    if (o.workspace) {
+      p->tab_keys = (int32_t*)(p->ws + p->lay.tab_keys);
+      p->tab_vals = (float*)(p->ws + p->lay.tab_vals);
+    } else {
+      const size_t kb = align256(sizeof(int32_t) * (size_t)slots);
+      LPA_CUDA(cudaMallocAsync((void**)&p->tab_ws, kb + sizeof(float) * (size_t)slots, s));
+      p->own_tab = true;
+      p->tab_keys = (int32_t*)p->tab_ws;
+      p->tab_vals = (float*)(p->tab_ws + kb);
+    }
+  }
+  return LPA_OK;
 }
 
 lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const float* weights,
@@ -203,6 +320,8 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
   if (o.leaf_max < 1 || o.leaf_max > kMaxLeaves || (o.leaf_max & (o.leaf_max - 1)))
     return fail(LPA_EINVAL, "leaf_max = %d must be a power of two in [1, %d]", o.leaf_max, kMaxLeaves);
+  if (((uintptr_t)indices & 15) != 0 || ((uintptr_t)weights & 15) != 0)
+    return fail(LPA_EINVAL, "indices and weights must be 16-byte aligned");
 
   lpa_plan_s* p = new lpa_plan_s();
   p->off = offsets;
@@ -226,12 +345,11 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   cudaError_t ce = cudaMallocHost((void**)&p->host_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_dn, sizeof(unsigned long long) * LPA_MAX_ITER);
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_q, sizeof(double) * 4);
-  if (ce != cudaSuccess)
-    return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_cls, sizeof(unsigned long long) * 32);
+  if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
 
   // workspace: fixed part now; exact-mode hub tables once binning knows their size
-  const int64_t tab_bound = p->mode == kExact ? 2 * m : 0;
-  p->lay = layout(n, m, p->mode, tab_bound);
+  p->lay = layout(n, p->mode, p->mode == kExact ? 2 * m : 0);
   if (o.workspace) {
     if (o.workspace_bytes < p->lay.total)
       return bail(fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, p->lay.total));
@@ -248,13 +366,14 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   }
   p->st = (DevState*)(p->ws + p->lay.state);
   p->dn = (unsigned long long*)(p->ws + p->lay.dn);
+  p->dn_total = (unsigned long long*)(p->ws + p->lay.dn_total);
   p->tmp = (int32_t*)(p->ws + p->lay.tmp);
-  p->cv0 = (int32_t*)(p->ws + p->lay.cv0);
-  p->cv1 = (int32_t*)(p->ws + p->lay.cv1);
-  p->hubs = (int32_t*)(p->ws + p->lay.hubs);
-  p->hub_tab = p->mode == kExact ? (int64_t*)(p->ws + p->lay.hub_tab) : nullptr;
-  int64_t* seg = (int64_t*)(p->ws + p->lay.seg);
-  const int64_t nseg = num_segments(n);
+  if (p->mode == kExact) {
+    p->cv0 = (int32_t*)(p->ws + p->lay.cv0);
+    p->cv1 = (int32_t*)(p->ws + p->lay.cv1);
+    p->hubs = (int32_t*)(p->ws + p->lay.hubs);
+    p->hub_tab = (int64_t*)(p->ws + p->lay.hub_tab);
+  }
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (p->flags & LPA_TIMING) {
@@ -281,52 +400,8 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
                        (err & kErrLabels) ? " labels_in out of range" : ""));
     }
   }
-
-  BinArgs b{};
-  b.off = offsets;
-  b.n = n;
-  b.cap = p->mode == kExact ? kChunkCapExact : kChunkCap;
-  b.cost_floor = b.cap / kThreads;
-  b.e0 = p->e0;
-  b.lmax = p->lmax;
-  b.leaves = p->mode == kExact ? 0 : 1;
-  b.seg_chunks = seg;
-  b.seg_hubs = seg + (nseg + 1);
-  b.seg_hub_edges = seg + 2 * (nseg + 1);
-  b.chunk_v0 = p->cv0;
-  b.chunk_v1 = p->cv1;
-  b.hubs = p->hubs;
-  b.hub_tab = p->hub_tab;
-  if (n > 0) {
-    ce = launch_bin(b, p->st, p->stream, false);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->stream);
-    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "binning: %s", cudaGetErrorString(ce)));
-    p->nchunks = p->host_state->nchunks;
-    p->nhubs = p->host_state->nhubs;
-    p->hub_edges = p->host_state->hub_edges;
-    if (p->nchunks + p->nhubs > 0x7fffffffLL || p->nchunks > n || p->nhubs > n)
-      return bail(fail(LPA_EINTERNAL, "binning produced %lld chunks and %lld hubs",
-                       (long long)p->nchunks, (long long)p->nhubs));
-    ce = launch_bin(b, p->st, p->stream, true);
-    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "binning: %s", cudaGetErrorString(ce)));
-  }
-  if (p->mode == kExact && p->hub_edges > 0) {
-    const int64_t slots = 2 * p->hub_edges;
-    if (o.workspace) {
-      p->tab_keys = (int32_t*)(p->ws + p->lay.tab_keys);
-      p->tab_vals = (float*)(p->ws + p->lay.tab_vals);
-    } else {
-      const size_t kb = align256(sizeof(int32_t) * (size_t)slots);
-      ce = cudaMallocAsync((void**)&p->tab_ws, kb + sizeof(float) * (size_t)slots, p->stream);
-      if (ce != cudaSuccess)
-        return bail(fail(LPA_ENOMEM, "cudaMallocAsync(hub tables): %s", cudaGetErrorString(ce)));
-      p->own_tab = true;
-      p->tab_keys = (int32_t*)p->tab_ws;
-      p->tab_vals = (float*)(p->tab_ws + kb);
-    }
-  }
+  s = p->mode == kExact ? bin_chunks(p, o) : bin_classes(p);
+  if (s != LPA_OK) return bail(s);
   if (p->flags & LPA_TIMING) {
     ce = cudaEventRecord(ev1, p->stream);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(ev1);
@@ -337,6 +412,17 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   }
   *out = p;
   return LPA_OK;
+}
+
+cudaError_t launch_plan_modularity(const lpa_plan_s* p, const int32_t* labels) {
+  double* sigma = (double*)(p->ws + p->lay.sigma);
+  double* partials = (double*)(p->ws + p->lay.partials);
+  double* out4 = (double*)(p->ws + p->lay.out4);
+  if (p->mode == kExact)
+    return launch_modularity(p->off, p->idx, p->w, labels, p->n, sigma, partials,
+                             modularity_partials(p->n), out4, p->stream);
+  return launch_modularity_plan(p->off, p->idx, p->w, p->m, labels, p->n, p->wp, sigma, partials,
+                                modularity_plan_partials(p->wp, p->n), out4, p->stream);
 }
 
 lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels_out,
@@ -362,29 +448,28 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
     if (es != LPA_OK) return es;
   }
   LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));  // done, iterations, converged, err
-  LPA_CUDA(launch_fill_u64(p->dn, 0ull, max_iter, s));
+  LPA_CUDA(launch_fill_u64(p->dn, 0ull, (int64_t)max_iter * kDnSlots, s));
   LPA_CUDA(launch_init_labels(labels_out, p->labels_in, n, s));
   int32_t* buf[2] = {labels_out, p->tmp};
   for (int l = 0; l < max_iter; ++l) {
     const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
-    SweepArgs a{};
-    sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less, p->dn + l, &p->st->done, &a);
+    const SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
+                                   p->dn + (int64_t)l * kDnSlots, &p->st->done);
     if (timing) LPA_CUDA(cudaEventRecord(p->events[2 + 2 * l], s));
-    LPA_CUDA(launch_sweep(p->mode, p->k, p->w != nullptr, a, s));
+    LPA_CUDA(launch_one_sweep(p, a));
     if (timing) LPA_CUDA(cudaEventRecord(p->events[3 + 2 * l], s));
-    LPA_CUDA(launch_converge(p->st, p->dn, l, pick_less, tol, n, s));
+    LPA_CUDA(launch_converge(p->st, p->dn, p->dn_total, l, pick_less, tol, n, s));
   }
   LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
   const bool want_q = (p->flags & LPA_MODULARITY) != 0;
   if (want_q) {
-    double* out4 = (double*)(p->ws + p->lay.out4);
-    LPA_CUDA(launch_modularity(p->off, p->idx, p->w, labels_out, n, (double*)(p->ws + p->lay.sigma),
-                               (double*)(p->ws + p->lay.partials), modularity_partials(n), out4, s));
-    LPA_CUDA(cudaMemcpyAsync(p->host_q, out4, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    LPA_CUDA(launch_plan_modularity(p, labels_out));
+    LPA_CUDA(cudaMemcpyAsync(p->host_q, p->ws + p->lay.out4, sizeof(double) * 4,
+                             cudaMemcpyDeviceToHost, s));
   }
   LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   if (max_iter > 0)
-    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn, sizeof(unsigned long long) * max_iter,
+    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn_total, sizeof(unsigned long long) * max_iter,
                              cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
   const int iters = p->host_state->iterations;
@@ -431,7 +516,7 @@ void lpa_options_init(lpa_options* opt) {
 size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k) {
   (void)k;
   if (n < 0 || m < 0) return 0;
-  return layout(n, m, (int)mode, mode == LPA_EXACT ? 2 * m : 0).total;
+  return layout(n, (int)mode, mode == LPA_EXACT ? 2 * m : 0).total;
 }
 
 size_t lpa_modularity_workspace_size(int32_t n) {
@@ -459,13 +544,13 @@ lpa_status lpa_plan_sweep(lpa_plan p, const int32_t* c_prev, int32_t* c_next, in
   const char* b0 = (const char*)c_next;
   const size_t bytes = sizeof(int32_t) * (size_t)p->n;
   if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(LPA_EINVAL, "c_prev and c_next overlap");
-  LPA_CUDA(launch_fill_u64(p->dn, 0ull, 1, p->stream));
-  SweepArgs a{};
-  sweep_args(p, c_prev, c_next, pick_less ? 1 : 0, p->dn, nullptr, &a);
-  LPA_CUDA(launch_sweep(p->mode, p->k, p->w != nullptr, a, p->stream));
+  LPA_CUDA(launch_fill_u64(p->dn, 0ull, kDnSlots, p->stream));
+  const SweepArgs a = sweep_args(p, c_prev, c_next, pick_less ? 1 : 0, p->dn, nullptr);
+  LPA_CUDA(launch_one_sweep(p, a));
   if (dn_out) {
-    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                             p->stream));
+    LPA_CUDA(launch_dn_sum(p->dn, p->dn_total, p->stream));
+    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn_total, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, p->stream));
     LPA_CUDA(cudaStreamSynchronize(p->stream));
     *dn_out = (int64_t)p->host_dn[0];
   }

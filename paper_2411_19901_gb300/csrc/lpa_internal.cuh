@@ -26,6 +26,19 @@ constexpr int kMaxWarpLeaves = 32;     // vertices with more leaves become hubs
 constexpr int kSegment = 2048;         // vertices per thread of the greedy binning
 constexpr int kMaxLeaves = 256;        // largest leaf_max accepted
 
+// Binning of the warp-per-row sweep (sketch modes).  Low rows (one leaf) are sorted by
+// degree inside windows of kWinVerts consecutive vertices; mid vertices (2..32 leaves)
+// fall into kMidClasses classes by leaf count and leaf length; hubs (rows longer than
+// kHubDegree or more than 32 leaves) get a CTA each.
+constexpr int kWinVerts = 4096;
+constexpr int kLowKeys = 1024;         // counting-sort keys (degree, capped)
+constexpr int kMidSub = 4;             // leaf-length quarters per leaf count
+constexpr int kMidClasses = 5 * kMidSub;
+constexpr int kHubClass = kMidClasses;
+constexpr int kNumClasses = kMidClasses + 1;
+constexpr int kHubDegree = 4096;
+constexpr int kDnSlots = 64;           // dN is spread over this many counters
+
 enum Mode { kExact = 0, kMG = 1, kBM = 2 };
 
 // Device-resident state of one run (lives at the start of the workspace).
@@ -60,6 +73,19 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
   return (int)(p < lmax ? p : lmax);
 }
 
+// Binned graph as the warp-per-row kernels see it.
+struct WarpPlan {
+  const int32_t* perm_low;  // per window: low rows sorted by degree (descending)
+  const int32_t* cnt_low;   // low rows per window
+  const int32_t* cls_list;  // mid classes then hubs
+  int64_t cls_start[kNumClasses + 1];
+  int32_t cls_warp_start[kMidClasses + 1];
+  int32_t nwin;
+  int32_t nhubs;
+  int32_t mid_ctas;
+  int32_t low_ctas;
+};
+
 // Arguments of one sweep launch.
 struct SweepArgs {
   const int64_t* off;
@@ -73,13 +99,14 @@ struct SweepArgs {
   const int64_t* hub_tab;  // exact mode: table offset of each hub
   int32_t* tab_keys;       // exact mode: hub tables (global)
   float* tab_vals;
-  unsigned long long* dn;  // dN counter of this sweep
+  unsigned long long* dn;  // dN counters of this sweep (kDnSlots for the warp kernels)
   const int32_t* done;     // skip the sweep if *done (null: never)
   int32_t nchunks;
   int32_t nhubs;
   int32_t pick_less;
   int32_t e0;
   int32_t lmax;
+  int64_t m;
 };
 
 // Arguments of the degree binning.
@@ -100,17 +127,37 @@ struct BinArgs {
 };
 
 // Host-side launchers (stream-ordered, no synchronisation).
-cudaError_t launch_sweep(int mode, int k, bool weighted, const SweepArgs& a,
-                         cudaStream_t s);
-size_t sweep_smem_bytes(int mode, bool weighted);
+// Sketch modes (MG, BM): warp-per-row kernel over a WarpPlan.
+cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
+                              const WarpPlan& p, cudaStream_t s);
+cudaError_t launch_sweep_mg_wide(int k, bool weighted, const SweepArgs& a, const WarpPlan& p,
+                                 cudaStream_t s);
+// Exact mode: chunk kernel over the chunk/hub binning.
+cudaError_t launch_sweep_exact(bool weighted, const SweepArgs& a, cudaStream_t s);
+size_t exact_smem_bytes(bool weighted);
+// Binning for the warp-per-row kernels: counts per class, then the lists.
+cudaError_t launch_classify(const int64_t* off, int32_t n, int e0, int lmax,
+                            unsigned long long* counts, int32_t* perm_low, int32_t* cnt_low,
+                            int32_t* cls_list, unsigned long long* cursors, bool fill,
+                            cudaStream_t s);
+// Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.
+cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const float* w,
+                                   int64_t m, const int32_t* labels, int32_t n,
+                                   const WarpPlan& p, double* sigma_c, double* partials,
+                                   int64_t npart, double* out4, cudaStream_t s);
+int64_t modularity_plan_partials(const WarpPlan& p, int32_t n);
+cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* out,
+                          cudaStream_t s);
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w,
                             int32_t n, int64_t m, const int32_t* labels_in, int32_t* err,
                             cudaStream_t s);
 cudaError_t launch_bin(const BinArgs& b, DevState* st, cudaStream_t s, bool write_pass);
 cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n,
                                cudaStream_t s);
-cudaError_t launch_converge(DevState* st, const unsigned long long* dn, int l,
-                            int pick_less, double tol, int32_t n, cudaStream_t s);
+// dn: kDnSlots counters per iteration; the test sums iteration l's slots into dn_total[l].
+cudaError_t launch_converge(DevState* st, const unsigned long long* dn,
+                            unsigned long long* dn_total, int l, int pick_less, double tol,
+                            int32_t n, cudaStream_t s);
 cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp,
                             int32_t n, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s);

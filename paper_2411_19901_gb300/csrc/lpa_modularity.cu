@@ -1,0 +1,203 @@
+// lpa_modularity.cu -- modularity (Sec. 3.2, Eq. 1) over the binned graph of a run:
+// Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2, accumulated in fp64.
+//
+// The rows pass reuses the sweep's work map (hub CTAs, mid leaf groups, degree-sorted
+// low rows) and its pipelined row reads, so it streams the CSR at the sweep's rate.
+// Per vertex it forms K_i (all entries, self-loops included, as stored) and the weight of
+// entries whose neighbour shares the label; Sigma_c receives K_i through one atomic per
+// run of equal labels in a warp.  Block sums go to kModSlots accumulators.
+#include "lpa_fold.cuh"
+
+namespace lpa {
+namespace {
+
+constexpr int kModSlots = 4096;
+constexpr int kSqBlocks = 152 * 8;
+
+// Row accumulator driven by fold_range: add(C[j], w) for every entry with w > 0.
+struct ModAcc {
+  double kv;
+  double in;
+  int cv;
+  __device__ __forceinline__ void add(int c, float w) {
+    kv += (double)w;
+    in += (c == cv) ? (double)w : 0.0;
+  }
+};
+
+__device__ __forceinline__ double warp_down_sum(double x, int width_mask_lane, int L) {
+  (void)width_mask_lane;
+  for (int s = 1; s < L; s <<= 1) {
+    const double y = __shfl_down_sync(kFullMask, x, s);
+    x += y;  // lanes that are not group leaders hold partial garbage, never read
+  }
+  return x;
+}
+
+template <bool WT>
+__global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
+    const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
+    const float* __restrict__ wts, int64_t m, const int32_t* __restrict__ labels, WarpPlan p,
+    double* sigma_c, double* slots) {
+  __shared__ double s_k[kThreads], s_in[kThreads];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const Work wk = lane_work(p, (int)blockIdx.x, tid >> 5, lane);
+  ModAcc acc{0.0, 0.0, -1};
+  bool owner = false;  // this thread ends holding a vertex total
+  int v = -1;
+  if (wk.kind == 0) {
+    v = wk.v;
+    const int64_t base = off[v];
+    const int64_t d = off[v + 1] - base;
+    const int L = leaf_count(d, 1, kThreads);  // split the row over all threads
+    acc.cv = labels[v];
+    if (tid < L)
+      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (tid * d) / L,
+                                    base + ((tid + 1) * d) / L);
+    s_k[tid] = acc.kv;
+    s_in[tid] = acc.in;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {  // fixed-order tree
+      if (tid < s) {
+        s_k[tid] += s_k[tid + s];
+        s_in[tid] += s_in[tid + s];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      acc.kv = s_k[0];
+      acc.in = s_in[0];
+      owner = true;
+    }
+    __syncthreads();
+  } else if (wk.kind > 0) {
+    v = wk.v;
+    if (v >= 0) {
+      acc.cv = labels[v];
+      const int64_t base = off[v];
+      const int64_t d = off[v + 1] - base;
+      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (wk.leaf * d) / wk.L,
+                                    base + ((wk.leaf + 1) * d) / wk.L);
+    }
+    if (wk.L > 1) {
+      acc.kv = warp_down_sum(acc.kv, 0, wk.L);
+      acc.in = warp_down_sum(acc.in, 0, wk.L);
+    }
+    owner = v >= 0 && wk.leaf == 0;
+  }
+  // Sigma_c: lanes of one warp with the same label add through their lowest lane
+  const int key = owner ? acc.cv : -(lane + 2);
+  const unsigned grp = __match_any_sync(kFullMask, key);
+  s_k[tid] = owner ? acc.kv : 0.0;
+  __syncwarp();
+  if (owner && lane == __ffs(grp) - 1) {
+    double sum = 0.0;
+    for (unsigned g = grp; g; g &= g - 1) sum += s_k[(tid & ~31) + __ffs(g) - 1];
+    if (sum != 0.0) atomicAdd(sigma_c + acc.cv, sum);
+  }
+  __syncthreads();
+  // block totals of K_i and of intra-community weight
+  s_k[tid] = owner ? acc.kv : 0.0;
+  s_in[tid] = owner ? acc.in : 0.0;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      s_k[tid] += s_k[tid + s];
+      s_in[tid] += s_in[tid + s];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && (s_k[0] != 0.0 || s_in[0] != 0.0)) {
+    const int slot = blockIdx.x & (kModSlots - 1);
+    atomicAdd(slots + 2 * slot, s_k[0]);
+    atomicAdd(slots + 2 * slot + 1, s_in[0]);
+  }
+}
+
+__global__ void zero_f64_kernel(double* p, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) sigma_sq_kernel(const double* sigma_c, int32_t n,
+                                                      double* sq) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * 256;
+  for (int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x; c < n; c += stride)
+    acc += sigma_c[c] * sigma_c[c];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sq[blockIdx.x] = s[0];
+}
+
+// Fixed-order final sums; out4 = {2m, intra weight, sum_c Sigma_c^2, Q}.
+__global__ void __launch_bounds__(256) modularity_total_kernel(const double* slots,
+                                                              const double* sq, double* out4) {
+  __shared__ double sa[256], sb[256], sc[256];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < kModSlots; i += 256) {
+    a += slots[2 * i];
+    b += slots[2 * i + 1];
+  }
+  for (int i = threadIdx.x; i < kSqBlocks; i += 256) c += sq[i];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sb[threadIdx.x] += sb[threadIdx.x + h];
+      sc[threadIdx.x] += sc[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double two_m = sa[0];
+    out4[0] = two_m;
+    out4[1] = sb[0];
+    out4[2] = sc[0];
+    out4[3] = two_m > 0.0 ? sb[0] / two_m - sc[0] / (two_m * two_m) : 0.0;
+  }
+}
+
+}  // namespace
+
+int64_t modularity_plan_partials(const WarpPlan& p, int32_t n) {
+  (void)p;
+  (void)n;
+  return 2 * (int64_t)kModSlots + kSqBlocks;
+}
+
+cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const float* w,
+                                   int64_t m, const int32_t* labels, int32_t n,
+                                   const WarpPlan& p, double* sigma_c, double* partials,
+                                   int64_t npart, double* out4, cudaStream_t s) {
+  (void)npart;
+  double* slots = partials;
+  double* sq = partials + 2 * kModSlots;
+  zero_f64_kernel<<<152 * 4, 256, 0, s>>>(sigma_c, n);
+  count_launch();
+  zero_f64_kernel<<<16, 256, 0, s>>>(slots, 2 * kModSlots);
+  count_launch();
+  const unsigned grid = (unsigned)(p.nhubs + p.mid_ctas + p.low_ctas);
+  if (grid > 0) {
+    if (w)
+      modularity_plan_kernel<true><<<grid, kThreads, 0, s>>>(off, idx, w, m, labels, p, sigma_c, slots);
+    else
+      modularity_plan_kernel<false><<<grid, kThreads, 0, s>>>(off, idx, w, m, labels, p, sigma_c, slots);
+    count_launch();
+  }
+  sigma_sq_kernel<<<kSqBlocks, 256, 0, s>>>(sigma_c, n, sq);
+  count_launch();
+  modularity_total_kernel<<<1, 256, 0, s>>>(slots, sq, out4);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace lpa

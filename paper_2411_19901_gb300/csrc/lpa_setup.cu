@@ -175,6 +175,109 @@ __global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t
   }
 }
 
+// ------------------------------------------------- binning for the warp sweep
+
+// Class of a vertex with d positions: -1 low (one leaf; *key = capped degree for the
+// window sort), [0, kMidClasses) mid (2..32 leaves; larger L and longer leaves first),
+// kHubClass for rows longer than kHubDegree or with more than 32 leaves.
+__device__ __forceinline__ int vertex_class(int64_t d, int e0, int lmax, int* key) {
+  const int L = leaf_count(d, e0, lmax);
+  if (d > kHubDegree || L > kMaxWarpLeaves) return kHubClass;
+  if (L == 1) {
+    *key = (int)(d < kLowKeys ? d : kLowKeys - 1);
+    return -1;
+  }
+  const int lidx = 5 - (31 - __clz(L));  // L = 32 -> 0 ... L = 2 -> 4
+  int sub = (int)(((d / L) * 4) / e0) - 4;  // leaf length quarter in [e0, 2 e0)
+  sub = sub < 0 ? 0 : (sub > kMidSub - 1 ? kMidSub - 1 : sub);
+  return lidx * kMidSub + (kMidSub - 1 - sub);
+}
+
+constexpr int kClassifyThreads = 1024;
+
+__global__ void __launch_bounds__(kClassifyThreads) classify_count_kernel(
+    const int64_t* off, int32_t n, int e0, int lmax, unsigned long long* counts) {
+  __shared__ unsigned int s_cnt[kNumClasses];
+  if (threadIdx.x < kNumClasses) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t v0 = (int64_t)blockIdx.x * kWinVerts;
+  for (int i = threadIdx.x; i < kWinVerts; i += kClassifyThreads) {
+    const int64_t v = v0 + i;
+    if (v >= n) break;
+    int key;
+    const int c = vertex_class(off[v + 1] - off[v], e0, lmax, &key);
+    if (c >= 0) atomicAdd(&s_cnt[c], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumClasses && s_cnt[threadIdx.x])
+    atomicAdd(counts + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// One CTA per window: low rows are counting-sorted by degree (descending) into the
+// window's slice of perm_low; mid and hub vertices are appended to their class lists
+// (cursors start at each class's offset).  Order inside a key or class does not matter.
+__global__ void __launch_bounds__(kClassifyThreads) classify_fill_kernel(
+    const int64_t* off, int32_t n, int e0, int lmax, int32_t* perm_low, int32_t* cnt_low,
+    int32_t* cls_list, unsigned long long* cursors) {
+  __shared__ int s_hist[kLowKeys];
+  __shared__ unsigned int s_cnt[kNumClasses];
+  __shared__ unsigned long long s_base[kNumClasses];
+  __shared__ int s_wsum[kClassifyThreads / 32];
+  constexpr int kPer = kWinVerts / kClassifyThreads;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kLowKeys; i += kClassifyThreads) s_hist[i] = 0;
+  if (tid < kNumClasses) s_cnt[tid] = 0;
+  __syncthreads();
+  const int64_t v0 = (int64_t)blockIdx.x * kWinVerts;
+  int cls[kPer], key[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t v = v0 + tid + q * kClassifyThreads;
+    cls[q] = -2;
+    key[q] = 0;
+    if (v < n) {
+      cls[q] = vertex_class(off[v + 1] - off[v], e0, lmax, &key[q]);
+      if (cls[q] == -1)
+        atomicAdd(&s_hist[key[q]], 1);
+      else
+        atomicAdd(&s_cnt[cls[q]], 1u);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the histogram in descending key order: thread t owns key K-1-t
+  const int k = kLowKeys - 1 - tid;
+  const int x = (tid < kLowKeys) ? s_hist[k] : 0;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((tid & 31) >= o) incl += y;
+  }
+  if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
+  if (tid < kNumClasses) s_base[tid] = s_cnt[tid] ? atomicAdd(cursors + tid, (unsigned long long)s_cnt[tid]) : 0;
+  __syncthreads();
+  int wpre = 0;
+  for (int w = 0; w < (tid >> 5); ++w) wpre += s_wsum[w];
+  if (tid < kLowKeys) s_hist[k] = wpre + incl - x;  // becomes the key's cursor
+  if (tid == kClassifyThreads - 1) {
+    int tot = 0;
+    for (int w = 0; w < kClassifyThreads / 32; ++w) tot += s_wsum[w];
+    cnt_low[blockIdx.x] = tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t v = v0 + tid + q * kClassifyThreads;
+    if (cls[q] == -1) {
+      const int pos = atomicAdd(&s_hist[key[q]], 1);
+      perm_low[v0 + pos] = (int32_t)v;
+    } else if (cls[q] >= 0) {
+      const unsigned long long pos = atomicAdd(&s_base[cls[q]], 1ull);
+      cls_list[pos] = (int32_t)v;
+    }
+  }
+}
+
 // ------------------------------------------------------------ driver helpers
 
 __global__ void init_labels_kernel(int32_t* c, const int32_t* labels_in, int32_t n) {
@@ -183,15 +286,27 @@ __global__ void init_labels_kernel(int32_t* c, const int32_t* labels_in, int32_t
     c[v] = labels_in ? labels_in[v] : (int32_t)v;
 }
 
-// Convergence test after sweep l (Alg. 1): stop iff pick-less was off and dN/N < tau.
-__global__ void converge_kernel(DevState* st, const unsigned long long* dn, int l, int pick_less,
-                                double tol, int32_t n) {
+// Convergence test after sweep l (Alg. 1): dN is the sum of the sweep's counters; stop
+// iff pick-less was off and dN/N < tau.
+__global__ void converge_kernel(DevState* st, const unsigned long long* dn,
+                                unsigned long long* dn_total, int l, int pick_less, double tol,
+                                int32_t n) {
   if (threadIdx.x != 0 || st->done) return;
+  unsigned long long tot = 0;
+  for (int i = 0; i < kDnSlots; ++i) tot += dn[(int64_t)l * kDnSlots + i];
+  dn_total[l] = tot;
   st->iterations = l + 1;
-  if (!pick_less && (double)dn[l] / (double)n < tol) {
+  if (!pick_less && (double)tot / (double)n < tol) {
     st->done = 1;
     st->converged = 1;
   }
+}
+
+__global__ void dn_sum_kernel(const unsigned long long* slots, unsigned long long* out) {
+  if (threadIdx.x != 0) return;
+  unsigned long long tot = 0;
+  for (int i = 0; i < kDnSlots; ++i) tot += slots[i];
+  *out = tot;
 }
 
 // Iteration l writes buffer (l+1) & 1; buffer 0 is the caller's output.
@@ -223,7 +338,9 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Pass 1 (warp per vertex): K_i and intra-community weight; Sigma_c += K_i.
+// Pass 1: a warp walks 32 consecutive vertices at a time, lanes striding over each row:
+// K_i and the intra-community weight; Sigma_c += K_i, with consecutive vertices of the
+// same label merged into one atomic (labels of neighbouring ids usually agree).
 __global__ void __launch_bounds__(kModThreads) modularity_rows_kernel(
     const int64_t* off, const int32_t* idx, const float* w, const int32_t* labels, int32_t n,
     double* sigma_c, double* partials) {
@@ -231,23 +348,35 @@ __global__ void __launch_bounds__(kModThreads) modularity_rows_kernel(
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (kModThreads / 32);
   double acc_k = 0.0, acc_in = 0.0;
-  for (int64_t v = (int64_t)blockIdx.x * (kModThreads / 32) + wid; v < n; v += nwarps) {
-    const int cv = labels[v];
-    double kv = 0.0, in = 0.0;
-    for (int64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
-      const double x = w ? (double)w[p] : 1.0;
-      kv += x;
-      if (labels[idx[p]] == cv) in += x;
-    }
-    kv = warp_sum(kv);
-    in = warp_sum(in);
-    if (lane == 0) {
-      if (kv != 0.0) atomicAdd(sigma_c + cv, kv);
-      acc_k += kv;
-      acc_in += in;
+  int run_c = -1;
+  double run_s = 0.0;
+  for (int64_t base = ((int64_t)blockIdx.x * (kModThreads / 32) + wid) * 32; base < n;
+       base += nwarps * 32) {
+    const int64_t vend = base + 32 < n ? base + 32 : n;
+    for (int64_t v = base; v < vend; ++v) {
+      const int cv = labels[v];
+      double kv = 0.0, in = 0.0;
+      for (int64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
+        const double x = w ? (double)w[p] : 1.0;
+        kv += x;
+        if (labels[idx[p]] == cv) in += x;
+      }
+      kv = warp_sum(kv);
+      in = warp_sum(in);
+      if (lane == 0) {
+        if (cv != run_c) {
+          if (run_c >= 0 && run_s != 0.0) atomicAdd(sigma_c + run_c, run_s);
+          run_c = cv;
+          run_s = 0.0;
+        }
+        run_s += kv;
+        acc_k += kv;
+        acc_in += in;
+      }
     }
   }
   if (lane == 0) {
+    if (run_c >= 0 && run_s != 0.0) atomicAdd(sigma_c + run_c, run_s);
     s_k[wid] = acc_k;
     s_in[wid] = acc_in;
   }
@@ -346,9 +475,10 @@ cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_converge(DevState* st, const unsigned long long* dn, int l, int pick_less,
-                            double tol, int32_t n, cudaStream_t s) {
-  converge_kernel<<<1, 32, 0, s>>>(st, dn, l, pick_less, tol, n);
+cudaError_t launch_converge(DevState* st, const unsigned long long* dn,
+                            unsigned long long* dn_total, int l, int pick_less, double tol,
+                            int32_t n, cudaStream_t s) {
+  converge_kernel<<<1, 32, 0, s>>>(st, dn, dn_total, l, pick_less, tol, n);
   count_launch();
   return cudaGetLastError();
 }
@@ -372,6 +502,28 @@ cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long value, int
                             cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   fill_u64_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* out,
+                          cudaStream_t s) {
+  dn_sum_kernel<<<1, 32, 0, s>>>(slots, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const int64_t* off, int32_t n, int e0, int lmax,
+                            unsigned long long* counts, int32_t* perm_low, int32_t* cnt_low,
+                            int32_t* cls_list, unsigned long long* cursors, bool fill,
+                            cudaStream_t s) {
+  const unsigned nwin = (unsigned)((n + kWinVerts - 1) / kWinVerts);
+  if (nwin == 0) return cudaSuccess;
+  if (!fill)
+    classify_count_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, n, e0, lmax, counts);
+  else
+    classify_fill_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, n, e0, lmax, perm_low, cnt_low,
+                                                           cls_list, cursors);
   count_launch();
   return cudaGetLastError();
 }
