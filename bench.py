@@ -410,6 +410,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "iterations": [s["iterations"] for s in stats],
+        "sweep_ms_iter": [round(x, 3) for x in stats[-1]["sweep_ms_iter"]],
         "modularity": stats[-1]["modularity"],
         "setup_ms": stats[-1]["setup_ms"],
         "generate_s": gen_s,

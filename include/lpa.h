@@ -74,6 +74,7 @@ typedef struct {
   int32_t chunks;                   /* CTA work units of the binned graph */
   int32_t hubs;                     /* vertices swept by a whole CTA */
   double modularity;                /* Q of the result (LPA_MODULARITY), else 0 */
+  float sweep_ms_iter[LPA_MAX_ITER]; /* device time of each sweep (LPA_TIMING) */
 } lpa_stats;
 
 /* Options.  Call lpa_options_init first; it sets the paper's defaults (Sec. 5.1.2). */

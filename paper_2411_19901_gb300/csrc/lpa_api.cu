@@ -51,7 +51,7 @@ int64_t num_windows(int64_t n) { return (n + kWinVerts - 1) / kWinVerts; }
 struct Layout {
   size_t state, dn, dn_total, tmp;
   // sketch modes
-  size_t perm_low, cnt_low, cls_list, counts, cursors;
+  size_t perm_low, cnt_low, low_desc, cls_list, counts, cursors;
   // exact mode
   size_t cv0, cv1, hubs, hub_tab, seg;
   // modularity
@@ -82,6 +82,7 @@ Layout layout(int64_t n, int mode, int64_t tab_slots) {
     const int64_t nwin = num_windows(n);
     L.perm_low = take(sizeof(int32_t) * (size_t)(nwin * kWinVerts));
     L.cnt_low = take(sizeof(int32_t) * (size_t)nwin);
+    L.low_desc = take(sizeof(int4) * (size_t)(nwin * kWinVerts));
     L.cls_list = take(sizeof(int32_t) * (size_t)n);
     L.counts = take(sizeof(unsigned long long) * 32);
     L.cursors = take(sizeof(unsigned long long) * 32);
@@ -134,6 +135,7 @@ struct lpa_plan_s {
   float* tab_vals = nullptr;
   int64_t nchunks = 0, nhubs = 0, hub_edges = 0;
   double setup_ms = 0.0;
+  bool exact_sums = false;  // every sum of a row's weights is exact in fp32
   std::vector<cudaEvent_t> events;  // timing pairs, created on demand
   DevState* host_state = nullptr;   // page-locked mirrors
   unsigned long long* host_dn = nullptr;
@@ -188,7 +190,7 @@ SweepArgs sweep_args(const lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next
 
 cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
   if (p->mode == kExact) return launch_sweep_exact(p->w != nullptr, a, p->stream);
-  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, a, p->wp, p->stream);
+  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream);
 }
 
 void destroy_plan(lpa_plan_s* p) {
@@ -218,11 +220,21 @@ lpa_status bin_classes(lpa_plan_s* p) {
   unsigned long long* counts = (unsigned long long*)(p->ws + p->lay.counts);
   unsigned long long* cursors = (unsigned long long*)(p->ws + p->lay.cursors);
   LPA_CUDA(launch_fill_u64(counts, 0ull, 32, s));
+  LPA_CUDA(launch_fill_u64(counts + kNumClasses, 1ull, 1, s));  // profile: all integral
   LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, counts, nullptr, nullptr, nullptr, nullptr,
                            false, s));
+  LPA_CUDA(launch_weight_profile(p->off, p->w, n, p->m, counts + kNumClasses, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 32,
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
+  {
+    const bool integral = p->host_cls[kNumClasses] != 0;
+    unsigned bits = (unsigned)p->host_cls[kNumClasses + 1];
+    float wmax;
+    memcpy(&wmax, &bits, sizeof(wmax));
+    const double dmax = (double)p->host_cls[kNumClasses + 2];
+    p->exact_sums = integral && (double)wmax * dmax <= 16777216.0;
+  }
   int64_t acc = 0;
   int64_t warps = 0;
   for (int c = 0; c < kNumClasses; ++c) {
@@ -240,14 +252,19 @@ lpa_status bin_classes(lpa_plan_s* p) {
   wp.cls_warp_start[kMidClasses] = (int32_t)warps;
   wp.nhubs = (int32_t)p->host_cls[kHubClass];
   wp.mid_ctas = (int32_t)((warps + (kThreads / 32) - 1) / (kThreads / 32));
-  wp.low_ctas = (int32_t)((int64_t)wp.nwin * (kWinVerts / kThreads));
-  const int64_t grid = (int64_t)wp.nhubs + wp.mid_ctas + wp.low_ctas;
-  if (grid > 0x7fffffffLL) return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
   for (int c = 0; c < kNumClasses; ++c) p->host_cls[c] = (unsigned long long)wp.cls_start[c];
   LPA_CUDA(cudaMemcpyAsync(cursors, p->host_cls, sizeof(unsigned long long) * kNumClasses,
                            cudaMemcpyHostToDevice, s));
   LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, nullptr, (int32_t*)wp.perm_low,
                            (int32_t*)wp.cnt_low, (int32_t*)wp.cls_list, cursors, true, s));
+  // low rows: one descriptor per sorted window slot
+  int4* desc = (int4*)(p->ws + p->lay.low_desc);
+  LPA_CUDA(launch_low_desc(p->off, wp.perm_low, wp.cnt_low, wp.nwin, desc, s));
+  wp.low_desc = desc;
+  wp.low_ctas = (int32_t)((int64_t)wp.nwin * (kWinVerts / kThreads));
+  const int64_t grid = (int64_t)wp.nhubs + wp.mid_ctas + wp.low_ctas;
+  if (grid > 0x7fffffffLL)
+    return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
   p->nhubs = wp.nhubs;
   p->nchunks = (int64_t)wp.mid_ctas + wp.low_ctas;
   return LPA_OK;
@@ -494,6 +511,11 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
         tot += ms;
       }
       stats->sweep_ms = tot;
+      for (int l = 0; l < iters; ++l) {
+        float ms = 0.f;
+        LPA_CUDA(cudaEventElapsedTime(&ms, p->events[2 + 2 * l], p->events[3 + 2 * l]));
+        stats->sweep_ms_iter[l] = ms;
+      }
     }
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }

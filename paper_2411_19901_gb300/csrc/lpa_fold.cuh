@@ -12,12 +12,15 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // ---------------------------------------------------------------- MG sketch
 
 // k-slot weighted Misra-Gries sketch held in registers (Sec. 4.1, Alg. 2).  Empty slots
-// hold key -1 and value 0; labels are >= 0, so a key only matches an occupied slot.
+// hold key -1 and value 0; labels are >= 0, so a key only matches an occupied slot.  em
+// is the bitmask of empty slots, kept up to date so the insert path needs no scan.
 template <int K>
 struct MGSketch {
   int key[K];
   float val[K];
+  unsigned em;
   static constexpr int kSlots = K;
+  static constexpr bool kRunMergeable = true;
 
   __device__ __forceinline__ void init(int /*own*/) {
 #pragma unroll
@@ -25,18 +28,13 @@ struct MGSketch {
       key[s] = -1;
       val[s] = 0.f;
     }
+    em = (K == 32) ? 0xffffffffu : ((1u << K) - 1u);
   }
 
-  __device__ __forceinline__ unsigned empty_mask() const {
-    unsigned em = 0;
-#pragma unroll
-    for (int s = 0; s < K; ++s) em |= (val[s] == 0.f ? 1u : 0u) << s;
-    return em;
-  }
-
-  // (c, w) into the lowest free slot named by the non-zero mask em
-  __device__ __forceinline__ void place(unsigned em, int c, float w) {
+  // (c, w) into the lowest free slot; em must be non-zero
+  __device__ __forceinline__ void place(int c, float w) {
     const int s0 = __ffs(em) - 1;
+    em &= em - 1u;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
       key[s] = (s == s0) ? c : key[s];
@@ -46,36 +44,38 @@ struct MGSketch {
 
   // sketchAccumulate with the clamped decrement: add to a matching slot, else fill the
   // lowest free slot, else lower every slot and w by min(w, smallest slot) and put a
-  // positive remainder in the lowest slot that became free
+  // positive remainder in the lowest slot that became free.  One insert site serves
+  // both the free-slot and the after-decrement case, so diverged lanes share it.
   __device__ __forceinline__ void add(int c, float w) {
     bool hit = false;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
       const bool m = (key[s] == c);
-      val[s] = m ? val[s] + w : val[s];
+      if (m) val[s] = val[s] + w;
       hit = hit || m;
     }
     if (hit) return;
-    unsigned em = empty_mask();
-    if (em) {
-      place(em, c, w);
-      return;
+    if (em == 0u) {
+      float lo[K];
+#pragma unroll
+      for (int s = 0; s < K; ++s) lo[s] = val[s];
+#pragma unroll
+      for (int h = K / 2; h >= 1; h /= 2)
+#pragma unroll
+        for (int s = 0; s < h; ++s) lo[s] = fminf(lo[s], lo[s + h]);
+      const float delta = fminf(w, lo[0]);
+      unsigned z = 0;
+#pragma unroll
+      for (int s = 0; s < K; ++s) {
+        val[s] = val[s] - delta;
+        const bool zero = (val[s] == 0.f);
+        if (zero) key[s] = -1;
+        z |= (zero ? 1u : 0u) << s;
+      }
+      em = z;
+      w = w - delta;
     }
-    float lo[K];
-#pragma unroll
-    for (int s = 0; s < K; ++s) lo[s] = val[s];
-#pragma unroll
-    for (int h = K / 2; h >= 1; h /= 2)
-#pragma unroll
-      for (int s = 0; s < h; ++s) lo[s] = fminf(lo[s], lo[s + h]);
-    const float delta = fminf(w, lo[0]);
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
-      val[s] = val[s] - delta;
-      key[s] = (val[s] == 0.f) ? -1 : key[s];
-    }
-    w = w - delta;
-    if (w > 0.f) place(empty_mask(), c, w);
+    if (w > 0.f) place(c, w);
   }
 
   // merge(A = this, B): B's occupied slots in ascending slot order (Sec. 4.3)
@@ -119,10 +119,12 @@ struct MGSketch {
     }
   }
   __device__ __forceinline__ void load(const int* k, const float* v) {
+    em = 0;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
       key[s] = k[s];
       val[s] = v[s];
+      em |= (v[s] == 0.f ? 1u : 0u) << s;
     }
   }
 };
@@ -135,6 +137,7 @@ struct BMState {
   int c;
   float w;
   static constexpr int kSlots = 1;
+  static constexpr bool kRunMergeable = false;
 
   __device__ __forceinline__ void init(int own) {
     c = own;
@@ -175,87 +178,148 @@ struct BMState {
 
 // ------------------------------------------------------------ pipelined row fold
 
-// Load the aligned group of four CSR positions starting at g (a multiple of 4).
-// Positions outside [b, e) come back with index `self` and weight 0, so the caller
-// skips them.  A group that would cross the end of the arrays is read element-wise.
+// Load the aligned group of four CSR positions starting at g (a multiple of 4).  A group
+// that would cross the end of the arrays is read element-wise; positions past the end
+// come back as (self, 0).  Which positions belong to the range is decided by the caller.
 template <bool WT>
 __device__ __forceinline__ void load_group(const int32_t* __restrict__ idx,
                                            const float* __restrict__ wts, int64_t m, int64_t g,
-                                           int64_t b, int64_t e, int self, int4& J, float4& W) {
-  int j[4];
-  float w[4];
+                                           int self, int4& J, float4& W) {
   if (g + 3 < m) {
-    const int4 jj = __ldg(reinterpret_cast<const int4*>(idx + g));
-    j[0] = jj.x, j[1] = jj.y, j[2] = jj.z, j[3] = jj.w;
-    if (WT) {
-      const float4 ww = __ldg(reinterpret_cast<const float4*>(wts + g));
-      w[0] = ww.x, w[1] = ww.y, w[2] = ww.z, w[3] = ww.w;
-    }
+    J = __ldg(reinterpret_cast<const int4*>(idx + g));
+    W = WT ? __ldg(reinterpret_cast<const float4*>(wts + g)) : make_float4(1.f, 1.f, 1.f, 1.f);
   } else {
+    int j[4];
+    float w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       j[u] = (g + u < m) ? __ldg(idx + g + u) : self;
-      if (WT) w[u] = (g + u < m) ? __ldg(wts + g + u) : 0.f;
+      w[u] = (g + u < m) ? (WT ? __ldg(wts + g + u) : 1.f) : 0.f;
     }
+    J = make_int4(j[0], j[1], j[2], j[3]);
+    W = make_float4(w[0], w[1], w[2], w[3]);
   }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const bool in = (g + u >= b) && (g + u < e);
-    if (!WT) w[u] = 1.f;
-    j[u] = in ? j[u] : self;
-    w[u] = in ? w[u] : 0.f;
-  }
-  J = make_int4(j[0], j[1], j[2], j[3]);
-  W = make_float4(w[0], w[1], w[2], w[3]);
+}
+
+// 4-bit mask of the group's positions that lie in [b, e)
+__device__ __forceinline__ unsigned group_mask(int64_t g, int64_t b, int64_t e) {
+  const int64_t lo = b - g;  // > 0 only for the first group
+  const int64_t hi = e - g;  // < 4 only for the last group
+  unsigned mk = 0xFu;
+  if (lo > 0) mk &= (0xFu << lo) & 0xFu;
+  if (hi < 4) mk &= 0xFu >> (4 - hi);
+  return mk;
 }
 
 // Neighbour labels of a group: -1 where the position is skipped (outside the range, a
 // self-loop when SKIP_SELF, or a weight that is not positive).
 template <bool SKIP_SELF>
 __device__ __forceinline__ int4 gather_group(const int32_t* __restrict__ lab, const int4& J,
-                                             const float4& W, int self) {
+                                             const float4& W, unsigned mk, int self) {
   int c[4];
   const int j[4] = {J.x, J.y, J.z, J.w};
   const float w[4] = {W.x, W.y, W.z, W.w};
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const bool use = (w[u] > 0.f) && (!SKIP_SELF || j[u] != self);
+    const bool use = ((mk >> u) & 1u) && (w[u] > 0.f) && (!SKIP_SELF || j[u] != self);
     c[u] = use ? __ldg(lab + j[u]) : -1;
   }
   return make_int4(c[0], c[1], c[2], c[3]);
 }
 
+// Feeds kept (label, weight) pairs into a state.  With RUNS, consecutive pairs of one
+// label are added as one pair of summed weight: for the Misra-Gries sketch with exact
+// arithmetic, add(c, a) then add(c, b) leaves the same slots as add(c, a + b) (a hit
+// adds both; an insert or a decrement followed by a hit or a re-insert ends with the
+// same remainder in the same slot), so the result is unchanged when every sum of the
+// row's weights is an exactly representable fp32 value.
+template <class S, bool RUNS>
+struct Feeder {
+  S& st;
+  int rc;
+  float rw;
+  __device__ __forceinline__ explicit Feeder(S& s) : st(s), rc(-1), rw(0.f) {}
+  __device__ __forceinline__ void push(int c, float w) {
+    if (c < 0) return;
+    if (!RUNS) {
+      st.add(c, w);
+      return;
+    }
+    if (c == rc) {
+      rw += w;
+    } else {
+      if (rc >= 0) st.add(rc, rw);
+      rc = c;
+      rw = w;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if (RUNS && rc >= 0) st.add(rc, rw);
+  }
+  __device__ __forceinline__ void reset() {
+    rc = -1;
+    rw = 0.f;
+  }
+};
+
 // Fold positions [b, e) of the CSR, in order, into st: st.add(C[j], w) for every kept
-// position.  Software pipeline: the index/weight group two ahead is loaded and the label
-// group one ahead is gathered before the current group is folded, so each lane keeps
-// eight loads and four gathers in flight while it works.
-template <class S, bool WT, bool SKIP_SELF>
+// position.  The range is read as aligned groups of four (16-byte index and weight
+// loads); only the first and last group carry a mask.  Software pipeline with three
+// register sets rotated by unrolling (no register moves): while group k is folded, the
+// labels of group k+1 are being gathered and group k+2 is being loaded.
+template <class S, bool WT, bool SKIP_SELF, bool RUNS = false>
 __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ idx,
                                            const float* __restrict__ wts,
                                            const int32_t* __restrict__ lab, int64_t m,
                                            int self, int64_t b, int64_t e) {
   if (b >= e) return;
-  int64_t g = b & ~(int64_t)3;
-  int4 J0, J1 = make_int4(self, self, self, self);
-  float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f);
-  load_group<WT>(idx, wts, m, g, b, e, self, J0, W0);
-  int4 C0 = gather_group<SKIP_SELF>(lab, J0, W0, self);
-  if (g + 4 < e) load_group<WT>(idx, wts, m, g + 4, b, e, self, J1, W1);
-  for (; g < e; g += 4) {
-    int4 C1 = make_int4(-1, -1, -1, -1);
-    if (g + 4 < e) C1 = gather_group<SKIP_SELF>(lab, J1, W1, self);
-    int4 J2 = make_int4(self, self, self, self);
-    float4 W2 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g + 8 < e) load_group<WT>(idx, wts, m, g + 8, b, e, self, J2, W2);
-    if (C0.x >= 0) st.add(C0.x, W0.x);
-    if (C0.y >= 0) st.add(C0.y, W0.y);
-    if (C0.z >= 0) st.add(C0.z, W0.z);
-    if (C0.w >= 0) st.add(C0.w, W0.w);
-    C0 = C1;
-    W0 = W1;
-    J1 = J2;
-    W1 = W2;
+  const int64_t g0 = b & ~(int64_t)3;
+  const int ng = (int)((e - g0 + 3) >> 2);
+  const unsigned first = (0xFu << (int)(b - g0)) & 0xFu;
+  const unsigned lastm = 0xFu >> (int)(g0 + 4 * (int64_t)ng - e);
+  const bool tail_unsafe = g0 + 4 * (int64_t)ng > m;  // last group crosses the array end
+  const int4* __restrict__ ip = reinterpret_cast<const int4*>(idx + g0);
+  const float4* __restrict__ wp = reinterpret_cast<const float4*>(wts + g0);
+  Feeder<S, RUNS> fd(st);
+
+  auto load = [&](int k, int4& X, float4& W) {
+    if (tail_unsafe && k == ng - 1) {
+      load_group<WT>(idx, wts, m, g0 + 4 * (int64_t)k, self, X, W);
+    } else {
+      X = __ldg(ip + k);
+      W = WT ? __ldg(wp + k) : make_float4(1.f, 1.f, 1.f, 1.f);
+    }
+  };
+  auto gather = [&](int k, int4& X, const float4& W) {
+    unsigned mk = 0xFu;
+    if (k == 0) mk &= first;
+    if (k == ng - 1) mk &= lastm;
+    X = gather_group<SKIP_SELF>(lab, X, W, mk, self);
+  };
+  auto fold = [&](const int4& C, const float4& W) {
+    fd.push(C.x, W.x);
+    fd.push(C.y, W.y);
+    fd.push(C.z, W.z);
+    fd.push(C.w, W.w);
+  };
+  int4 X0, X1 = make_int4(self, self, self, self), X2 = make_int4(self, self, self, self);
+  float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  load(0, X0, W0);
+  gather(0, X0, W0);
+  if (ng > 1) load(1, X1, W1);
+  // step k: F = group k (gathered), G = group k+1 (loaded), L = free
+#define LPA_STEP(XF, WF, XG, WG, XL, WL)   \
+  if (k + 1 < ng) gather(k + 1, XG, WG);   \
+  if (k + 2 < ng) load(k + 2, XL, WL);     \
+  fold(XF, WF);                            \
+  if (++k >= ng) break;
+  for (int k = 0;;) {
+    LPA_STEP(X0, W0, X1, W1, X2, W2)
+    LPA_STEP(X1, W1, X2, W2, X0, W0)
+    LPA_STEP(X2, W2, X0, W0, X1, W1)
   }
+#undef LPA_STEP
+  fd.flush();
 }
 
 // ------------------------------------------------------------ work decomposition
@@ -269,10 +333,13 @@ struct Work {
   int v;       // vertex (or -1 for an idle lane)
   int leaf;    // leaf index of this lane (mid), 0 otherwise
   int L;       // leaves of the vertex (mid: the class's L; low: 1)
+  int64_t b;   // row start and length (mid and low lanes with a vertex)
+  int64_t d;
 };
 
-__device__ __forceinline__ Work lane_work(const WarpPlan& p, int cta, int warp, int lane) {
-  Work w{-1, -1, 0, 1};
+__device__ __forceinline__ Work lane_work(const WarpPlan& p, const int64_t* __restrict__ off,
+                                          int cta, int warp, int lane) {
+  Work w{-1, -1, 0, 1, 0, 0};
   if (cta < p.nhubs) {
     w.kind = 0;
     w.v = p.cls_list[p.cls_start[kHubClass] + cta];
@@ -290,7 +357,11 @@ __device__ __forceinline__ Work lane_work(const WarpPlan& p, int cta, int warp, 
     const int64_t slot = (int64_t)(gw - p.cls_warp_start[c]) * (32 / L) + lane / L;
     const int64_t cnt = p.cls_start[c + 1] - p.cls_start[c];
     w.leaf = lane % L;
-    if (slot < cnt) w.v = p.cls_list[p.cls_start[c] + slot];
+    if (slot < cnt) {
+      w.v = p.cls_list[p.cls_start[c] + slot];
+      w.b = off[w.v];
+      w.d = off[w.v + 1] - w.b;
+    }
     return w;
   }
   cta -= p.mid_ctas;
@@ -299,7 +370,12 @@ __device__ __forceinline__ Work lane_work(const WarpPlan& p, int cta, int warp, 
   const int win = lw / (kWinVerts / 32);
   if (win >= p.nwin) return w;
   const int pos = (lw % (kWinVerts / 32)) * 32 + lane;
-  if (pos < p.cnt_low[win]) w.v = p.perm_low[(int64_t)win * kWinVerts + pos];
+  if (pos < p.cnt_low[win]) {
+    const int4 dsc = __ldg(p.low_desc + (int64_t)win * kWinVerts + pos);
+    w.v = dsc.x;
+    w.b = (int64_t)(uint32_t)dsc.y | ((int64_t)dsc.z << 32);
+    w.d = dsc.w;
+  }
   return w;
 }
 

@@ -77,13 +77,14 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
 struct WarpPlan {
   const int32_t* perm_low;  // per window: low rows sorted by degree (descending)
   const int32_t* cnt_low;   // low rows per window
+  const int4* low_desc;     // per window slot: {v, offset low, offset high, degree}
   const int32_t* cls_list;  // mid classes then hubs
   int64_t cls_start[kNumClasses + 1];
   int32_t cls_warp_start[kMidClasses + 1];
   int32_t nwin;
   int32_t nhubs;
   int32_t mid_ctas;
-  int32_t low_ctas;
+  int32_t low_ctas;         // nwin * kWinVerts / kThreads
 };
 
 // Arguments of one sweep launch.
@@ -128,10 +129,17 @@ struct BinArgs {
 
 // Host-side launchers (stream-ordered, no synchronisation).
 // Sketch modes (MG, BM): warp-per-row kernel over a WarpPlan.
-cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
+// runs: fold runs of equal labels as one add (MG; only when row sums are exact in fp32).
+cudaError_t launch_sweep_warp(int mode, int k, bool weighted, bool runs, const SweepArgs& a,
                               const WarpPlan& p, cudaStream_t s);
-cudaError_t launch_sweep_mg_wide(int k, bool weighted, const SweepArgs& a, const WarpPlan& p,
-                                 cudaStream_t s);
+cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s);
+cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s);
+// Weight profile: out[0] = 1 if every weight is integer-valued (AND), out[1] = largest
+// weight's bits, out[2] = largest row length.  out must be zeroed except out[0] = 1.
+cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
+                                  unsigned long long* out, cudaStream_t s);
 // Exact mode: chunk kernel over the chunk/hub binning.
 cudaError_t launch_sweep_exact(bool weighted, const SweepArgs& a, cudaStream_t s);
 size_t exact_smem_bytes(bool weighted);
@@ -146,6 +154,9 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
                                    const WarpPlan& p, double* sigma_c, double* partials,
                                    int64_t npart, double* out4, cudaStream_t s);
 int64_t modularity_plan_partials(const WarpPlan& p, int32_t n);
+// Low-row descriptors {v, offset, degree} for every sorted window slot.
+cudaError_t launch_low_desc(const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low,
+                            int32_t nwin, int4* desc, cudaStream_t s);
 cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* out,
                           cudaStream_t s);
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
     double* sigma_c, double* slots) {
   __shared__ double s_k[kThreads], s_in[kThreads];
   const int tid = threadIdx.x, lane = tid & 31;
-  const Work wk = lane_work(p, (int)blockIdx.x, tid >> 5, lane);
+  const Work wk = lane_work(p, off, (int)blockIdx.x, tid >> 5, lane);
   ModAcc acc{0.0, 0.0, -1};
   bool owner = false;  // this thread ends holding a vertex total
   int v = -1;
@@ -74,10 +74,8 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
     v = wk.v;
     if (v >= 0) {
       acc.cv = labels[v];
-      const int64_t base = off[v];
-      const int64_t d = off[v + 1] - base;
-      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (wk.leaf * d) / wk.L,
-                                    base + ((wk.leaf + 1) * d) / wk.L);
+      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, wk.b + (wk.leaf * wk.d) / wk.L,
+                                    wk.b + ((wk.leaf + 1) * wk.d) / wk.L);
     }
     if (wk.L > 1) {
       acc.kv = warp_down_sum(acc.kv, 0, wk.L);

@@ -278,6 +278,57 @@ __global__ void __launch_bounds__(kClassifyThreads) classify_fill_kernel(
   }
 }
 
+// Low-row descriptors: each sorted window slot's {v, offset (two halves), degree}, so a
+// sweep lane reads its row with one 16-byte load.
+__global__ void __launch_bounds__(kClassifyThreads) low_desc_kernel(
+    const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low, int4* desc) {
+  const int win = blockIdx.x;
+  const int cnt = cnt_low[win];
+  int4* d = desc + (int64_t)win * kWinVerts;
+  for (int pos = threadIdx.x; pos < cnt; pos += kClassifyThreads) {
+    const int v = perm_low[(int64_t)win * kWinVerts + pos];
+    const int64_t b = off[v];
+    d[pos] = make_int4(v, (int)(uint32_t)(b & 0xffffffffLL), (int)(b >> 32), (int)(off[v + 1] - b));
+  }
+}
+
+// Whether every sum of a row's weights is exact in fp32: integer-valued weights and
+// (longest row) x (largest weight) <= 2^24 suffice.
+__global__ void weight_profile_kernel(const int64_t* off, const float* w, int32_t n, int64_t m,
+                                      unsigned long long* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool integral = true;
+  unsigned wmax = 0;
+  long long dmax = 0;
+  if (w)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+      const float x = w[e];
+      integral = integral && (x == truncf(x));
+      const unsigned bits = __float_as_uint(x);  // weights are >= 0: bit order = value order
+      wmax = bits > wmax ? bits : wmax;
+    }
+  else
+    wmax = __float_as_uint(1.f);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const long long d = off[v + 1] - off[v];
+    dmax = d > dmax ? d : dmax;
+  }
+  if (!__all_sync(0xffffffffu, integral) && (threadIdx.x & 31) == 0) atomicAnd(out, 0ull);
+  unsigned wm = wmax;
+  long long dm = dmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned a = __shfl_down_sync(0xffffffffu, wm, o);
+    const long long b = __shfl_down_sync(0xffffffffu, dm, o);
+    wm = a > wm ? a : wm;
+    dm = b > dm ? b : dm;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out + 1, (unsigned long long)wm);
+    atomicMax(out + 2, (unsigned long long)dm);
+  }
+}
+
 // ------------------------------------------------------------ driver helpers
 
 __global__ void init_labels_kernel(int32_t* c, const int32_t* labels_in, int32_t n) {
@@ -524,6 +575,21 @@ cudaError_t launch_classify(const int64_t* off, int32_t n, int e0, int lmax,
   else
     classify_fill_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, n, e0, lmax, perm_low, cnt_low,
                                                            cls_list, cursors);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_low_desc(const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low,
+                            int32_t nwin, int4* desc, cudaStream_t s) {
+  if (nwin == 0) return cudaSuccess;
+  low_desc_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, perm_low, cnt_low, desc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
+                                  unsigned long long* out, cudaStream_t s) {
+  weight_profile_kernel<<<grid_for(m > n ? m : n, 256), 256, 0, s>>>(off, w, n, m, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -1,29 +1,21 @@
 // lpa_sweep.cu -- sweep kernels of the sketch modes: MG with k = 1, 2, 4, 8 and BM.
-// (k = 16 and 32 live in lpa_sweep_wide.cu so the two compile in parallel.)
+// (k = 16 and k = 32 live in lpa_sweep_k16.cu / lpa_sweep_k32.cu so they compile in
+// parallel.)
 #include "lpa_sweep_impl.cuh"
 
 namespace lpa {
 
-cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
+cudaError_t launch_sweep_warp(int mode, int k, bool weighted, bool runs, const SweepArgs& a,
                               const WarpPlan& p, cudaStream_t s) {
-  if (mode == kBM)
-    return weighted ? launch_warp_kernel<BMState, true>(a, p, s)
-                    : launch_warp_kernel<BMState, false>(a, p, s);
+  if (mode == kBM) return launch_warp_variants<BMState>(weighted, false, a, p, s);
   switch (k) {
-    case 1:
-      return weighted ? launch_warp_kernel<MGSketch<1>, true>(a, p, s)
-                      : launch_warp_kernel<MGSketch<1>, false>(a, p, s);
-    case 2:
-      return weighted ? launch_warp_kernel<MGSketch<2>, true>(a, p, s)
-                      : launch_warp_kernel<MGSketch<2>, false>(a, p, s);
-    case 4:
-      return weighted ? launch_warp_kernel<MGSketch<4>, true>(a, p, s)
-                      : launch_warp_kernel<MGSketch<4>, false>(a, p, s);
-    case 8:
-      return weighted ? launch_warp_kernel<MGSketch<8>, true>(a, p, s)
-                      : launch_warp_kernel<MGSketch<8>, false>(a, p, s);
-    default:
-      return launch_sweep_mg_wide(k, weighted, a, p, s);
+    case 1: return launch_warp_variants<MGSketch<1>>(weighted, runs, a, p, s);
+    case 2: return launch_warp_variants<MGSketch<2>>(weighted, runs, a, p, s);
+    case 4: return launch_warp_variants<MGSketch<4>>(weighted, runs, a, p, s);
+    case 8: return launch_warp_variants<MGSketch<8>>(weighted, runs, a, p, s);
+    case 16: return launch_sweep_mg16(weighted, runs, a, p, s);
+    case 32: return launch_sweep_mg32(weighted, runs, a, p, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

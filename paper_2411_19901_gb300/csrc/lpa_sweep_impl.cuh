@@ -44,16 +44,19 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
   }
 }
 
-template <class S, bool WT>
+// RUNS folds runs of equal consecutive labels as one add (MG only; the caller enables it
+// when every sum of a row's weights is exact in fp32, so the bits do not change).
+template <class S, bool WT, bool RUNS>
 __global__ void __launch_bounds__(kThreads) sweep_warp_kernel(SweepArgs a, WarpPlan p) {
+  constexpr bool kRuns = RUNS && S::kRunMergeable;
   if (a.done != nullptr && *a.done) return;
   __shared__ int sk[(kThreads / 32) * 32];
   __shared__ float sv[(kThreads / 32) * 32];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const Work wk = lane_work(p, (int)blockIdx.x, tid >> 5, lane);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int cta = (int)blockIdx.x;
   int changed = 0;
-  if (wk.kind == 0) {  // hub: the whole CTA
-    const int v = wk.v;
+  if (cta < p.nhubs) {  // hub: the whole CTA, one leaf per thread
+    const int v = p.cls_list[p.cls_start[kHubClass] + cta];
     const int64_t base = a.off[v];
     const int64_t d = a.off[v + 1] - base;
     const int L = leaf_count(d, a.e0, a.lmax);
@@ -61,8 +64,8 @@ __global__ void __launch_bounds__(kThreads) sweep_warp_kernel(SweepArgs a, WarpP
     S st;
     st.init(own);
     if (tid < L)
-      fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
-                              base + ((tid + 1) * d) / L);
+      fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
+                                     base + ((tid + 1) * d) / L);
     const int Lw = L < 32 ? L : 32;
     for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
     if (L > 32) cross_warp_tree<S>(st, L, tid, sk, sv);
@@ -71,42 +74,51 @@ __global__ void __launch_bounds__(kThreads) sweep_warp_kernel(SweepArgs a, WarpP
       a.c_next[v] = nl;
       changed = nl != own;
     }
-  } else if (wk.kind > 0) {  // mid leaf group or low row: one lane per leaf
+  } else {  // mid leaf group or low row: one lane per leaf
+    const Work wk = lane_work(p, a.off, cta, warp, lane);
     S st;
     int own = -1;
     if (wk.v >= 0) {
       own = a.c_prev[wk.v];
       st.init(own);
-      const int64_t base = a.off[wk.v];
-      const int64_t d = a.off[wk.v + 1] - base;
-      fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, wk.v, base + (wk.leaf * d) / wk.L,
-                              base + ((wk.leaf + 1) * d) / wk.L);
+      fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, wk.v,
+                                     wk.b + (wk.leaf * wk.d) / wk.L,
+                                     wk.b + ((wk.leaf + 1) * wk.d) / wk.L);
     } else {
       st.init(-1);
     }
-    for (int s = 1; s < wk.L; s <<= 1)
-      st.shfl_merge(s, wk.v >= 0 && (wk.leaf & (2 * s - 1)) == 0);
+    for (int s = 1; s < wk.L; s <<= 1) st.shfl_merge(s, wk.v >= 0 && (wk.leaf & (2 * s - 1)) == 0);
     if (wk.v >= 0 && wk.leaf == 0) {
       const int nl = commit_label(st.choose(), own, a.pick_less);
       a.c_next[wk.v] = nl;
       changed = nl != own;
     }
   }
-  const int cnt = __syncthreads_count(changed);
-  if (tid == 0 && cnt > 0) atomicAdd(a.dn + (blockIdx.x & (kDnSlots - 1)), (unsigned long long)cnt);
+  const int wsum = __reduce_add_sync(kFullMask, changed);
+  if (lane == 0 && wsum > 0)
+    atomicAdd(a.dn + ((blockIdx.x * (kThreads / 32) + warp) & (kDnSlots - 1)), (unsigned long long)wsum);
 }
 
 inline unsigned sweep_grid(const WarpPlan& p) {
   return (unsigned)(p.nhubs + p.mid_ctas + p.low_ctas);
 }
 
-template <class S, bool WT>
+template <class S, bool WT, bool RUNS>
 cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s) {
   const unsigned grid = sweep_grid(p);
   if (grid == 0) return cudaSuccess;
-  sweep_warp_kernel<S, WT><<<grid, kThreads, 0, s>>>(a, p);
+  sweep_warp_kernel<S, WT, RUNS><<<grid, kThreads, 0, s>>>(a, p);
   count_launch();
   return cudaGetLastError();
+}
+
+// The four instantiations of one sketch type: weighted or not, runs folded or not.
+template <class S>
+cudaError_t launch_warp_variants(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+                                 cudaStream_t s) {
+  if (weighted)
+    return runs ? launch_warp_kernel<S, true, true>(a, p, s) : launch_warp_kernel<S, true, false>(a, p, s);
+  return runs ? launch_warp_kernel<S, false, true>(a, p, s) : launch_warp_kernel<S, false, false>(a, p, s);
 }
 
 }  // namespace lpa

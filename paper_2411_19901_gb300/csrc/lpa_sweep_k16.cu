@@ -1,0 +1,11 @@
+// lpa_sweep_k16.cu -- sweep kernels of the MG mode with k = 16 slots.
+#include "lpa_sweep_impl.cuh"
+
+namespace lpa {
+
+cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s) {
+  return launch_warp_variants<MGSketch<16>>(weighted, runs, a, p, s);
+}
+
+}  // namespace lpa

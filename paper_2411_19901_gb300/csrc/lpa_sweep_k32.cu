@@ -1,0 +1,11 @@
+// lpa_sweep_k32.cu -- sweep kernels of the MG mode with k = 32 slots.
+#include "lpa_sweep_impl.cuh"
+
+namespace lpa {
+
+cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s) {
+  return launch_warp_variants<MGSketch<32>>(weighted, runs, a, p, s);
+}
+
+}  // namespace lpa

@@ -47,6 +47,7 @@ class lpa_stats(ctypes.Structure):
         ("chunks", ctypes.c_int32),
         ("hubs", ctypes.c_int32),
         ("modularity", ctypes.c_double),
+        ("sweep_ms_iter", ctypes.c_float * LPA_MAX_ITER),
     ]
 
     def to_dict(self) -> dict:
@@ -64,6 +65,7 @@ class lpa_stats(ctypes.Structure):
             "chunks": int(self.chunks),
             "hubs": int(self.hubs),
             "modularity": float(self.modularity),
+            "sweep_ms_iter": [float(x) for x in self.sweep_ms_iter[:it]],
         }
 
 
