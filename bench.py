@@ -38,10 +38,10 @@ import synth  # noqa: E402
 METRIC = "MG8-LPA edges/sec/iteration"
 UNIT = "edges/s"
 
-# DRAM traffic of one sweep launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the workload named below, scaled per launch, and the hash of
-# the sweep kernel source it was taken with.  If the source changes, traffic is reported
-# as null until a new capture is taken.
+# DRAM traffic of one sweep (its hub and lane kernels together) measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
+# hash of the sweep kernel source it was taken with.  If the source changes, traffic is
+# reported as null until a new capture is taken.
 SWEEP_TRAFFIC = {"src_sha256": None, "workload": None, "bytes_per_launch": None}
 
 WORKLOADS = {
@@ -400,7 +400,8 @@ def run_ours(args):
         "config": config_of(args, g),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "sweep_warp_kernel<MGSketch<8>, weighted>",
+                     "kernel": "one sweep: sweep_hub_kernel and sweep_lane_kernel "
+                               "<MGSketch<8>, weighted, runs> (concurrent, fork/join)",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,

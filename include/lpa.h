@@ -165,9 +165,14 @@ lpa_status lpa_modularity_noalloc(const int64_t* offsets, const int32_t* indices
                                   const int32_t* labels, double* q_out,
                                   const lpa_options* opt);
 
-/* Device workspace an lpa_detect_ex call needs (an upper bound for any graph with these
- * sizes); lpa_modularity_ex needs lpa_modularity_workspace_size(n). */
+/* Device workspace an lpa_detect_ex call needs: an upper bound for any graph with these
+ * sizes under the default options (leaf_e0 = 64).  The sketch modes' lane table grows as
+ * m / leaf_e0, so a call with a smaller leaf_e0 takes lpa_workspace_size_ex with its
+ * options (opt == NULL: the defaults).  Both return 0 for negative sizes or leaf_e0 < 1.
+ * lpa_modularity_ex needs lpa_modularity_workspace_size(n). */
 size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k);
+size_t lpa_workspace_size_ex(int32_t n, int64_t m, lpa_mode mode, int32_t k,
+                             const lpa_options* opt);
 size_t lpa_modularity_workspace_size(int32_t n);
 
 /* ---- Plans: bin a graph once, then run sweeps or whole runs on it. ---------------

@@ -6,6 +6,7 @@
 // on their first instruction.  The host synchronises once, at the end, to read the
 // statistics.  Sketch modes (MG, BM) run the warp-per-row sweep over a class binning;
 // the exact mode runs its chunk kernel over the chunk/hub binning.
+#include <algorithm>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -47,11 +48,25 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int64_t num_windows(int64_t n) { return (n + kWinVerts - 1) / kWinVerts; }
 
+// Bounds of the warp-per-row binning for leaf parameter e0 (see lpa_internal.cuh).  A hub
+// has more than kHubDegree positions or at least 64 leaves (so >= 64 e0 positions).  A mid
+// vertex of L leaves has L e0 <= d positions and L <= 32, so the lanes, one per low
+// vertex and L per mid vertex, number at most n + min(m / e0, 31 n), plus under a warp of
+// padding per window.
+int64_t hub_cap(int64_t n, int64_t m, int e0) {
+  const int64_t dmin = std::min<int64_t>(kHubDegree + 1, 64 * (int64_t)e0);
+  return std::min<int64_t>(n, m / dmin);
+}
+int64_t lane_cap(int64_t n, int64_t m, int e0) {
+  return n + std::min<int64_t>(m / e0, 31 * n) + 32 * num_windows(n);
+}
+
 // Workspace layout of a plan; offsets in bytes from the workspace base.
 struct Layout {
   size_t state, dn, dn_total, tmp;
   // sketch modes
-  size_t perm_low, cnt_low, low_desc, cls_list, counts, cursors;
+  size_t desc, wtab, hcnt, lcnt, hub_prefix, lane_prefix, hub_desc, lane_desc, counts;
+  int64_t hub_cap, lane_cap;
   // exact mode
   size_t cv0, cv1, hubs, hub_tab, seg;
   // modularity
@@ -59,7 +74,7 @@ struct Layout {
   size_t total_fixed, tab_keys, tab_vals, total;
 };
 
-Layout layout(int64_t n, int mode, int64_t tab_slots) {
+Layout layout(int64_t n, int64_t m, int mode, int e0, int64_t tab_slots) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -80,12 +95,17 @@ Layout layout(int64_t n, int mode, int64_t tab_slots) {
     L.partials = take(sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
   } else {
     const int64_t nwin = num_windows(n);
-    L.perm_low = take(sizeof(int32_t) * (size_t)(nwin * kWinVerts));
-    L.cnt_low = take(sizeof(int32_t) * (size_t)nwin);
-    L.low_desc = take(sizeof(int4) * (size_t)(nwin * kWinVerts));
-    L.cls_list = take(sizeof(int32_t) * (size_t)n);
-    L.counts = take(sizeof(unsigned long long) * 32);
-    L.cursors = take(sizeof(unsigned long long) * 32);
+    L.hub_cap = hub_cap(n, m, e0);
+    L.lane_cap = lane_cap(n, m, e0);
+    L.desc = take(sizeof(int4) * (size_t)(nwin * kWinVerts));
+    L.wtab = take(sizeof(int32_t) * (size_t)(nwin * kWinTab));
+    L.hcnt = take(sizeof(int32_t) * (size_t)nwin);
+    L.lcnt = take(sizeof(int32_t) * (size_t)nwin);
+    L.hub_prefix = take(sizeof(int64_t) * (size_t)(nwin + 1));
+    L.lane_prefix = take(sizeof(int64_t) * (size_t)(nwin + 1));
+    L.hub_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.hub_cap, 1));
+    L.lane_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.lane_cap, 1));
+    L.counts = take(sizeof(unsigned long long) * 8);
     WarpPlan dummy{};
     L.partials = take(sizeof(double) * (size_t)modularity_plan_partials(dummy, (int32_t)n));
   }
@@ -118,6 +138,8 @@ struct lpa_plan_s {
   uint32_t flags = 0;
   const int32_t* labels_in = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // sketch modes: the hub kernel runs here, beside the lanes
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool own_ws = false;
@@ -190,12 +212,26 @@ SweepArgs sweep_args(const lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next
 
 cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
   if (p->mode == kExact) return launch_sweep_exact(p->w != nullptr, a, p->stream);
-  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream);
+  if (!p->side)
+    return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
+                             p->stream);
+  // fork: the hub kernel on the side stream, the lane kernel on the plan's stream; join
+  cudaError_t e = cudaEventRecord(p->fork_ev, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork_ev, 0);
+  if (e == cudaSuccess)
+    e = launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
+                          p->side);
+  if (e == cudaSuccess) e = cudaEventRecord(p->join_ev, p->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->join_ev, 0);
+  return e;
 }
 
 void destroy_plan(lpa_plan_s* p) {
   if (!p) return;
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  if (p->join_ev) cudaEventDestroy(p->join_ev);
+  if (p->side) cudaStreamDestroy(p->side);
   if (p->own_ws && p->ws) cudaFreeAsync(p->ws, p->stream);
   if (p->own_tab && p->tab_ws) cudaFreeAsync(p->tab_ws, p->stream);
   if (p->own_ws || p->own_tab) cudaStreamSynchronize(p->stream);
@@ -206,67 +242,61 @@ void destroy_plan(lpa_plan_s* p) {
   delete p;
 }
 
-// Class binning of the sketch modes: count classes, lay out the lists, fill them.
+// Window binning of the sketch modes: sort each window's vertices into groups, lay out
+// the hub and lane descriptors, and read back the totals.
 lpa_status bin_classes(lpa_plan_s* p) {
   cudaStream_t s = p->stream;
   const int32_t n = p->n;
+  const Layout& ly = p->lay;
   WarpPlan& wp = p->wp;
   wp = WarpPlan{};
-  wp.perm_low = (const int32_t*)(p->ws + p->lay.perm_low);
-  wp.cnt_low = (const int32_t*)(p->ws + p->lay.cnt_low);
-  wp.cls_list = (const int32_t*)(p->ws + p->lay.cls_list);
-  wp.nwin = (int32_t)num_windows(n);
+  wp.hub_desc = (const int4*)(p->ws + ly.hub_desc);
+  wp.lane_desc = (const int4*)(p->ws + ly.lane_desc);
   if (n == 0) return LPA_OK;
-  unsigned long long* counts = (unsigned long long*)(p->ws + p->lay.counts);
-  unsigned long long* cursors = (unsigned long long*)(p->ws + p->lay.cursors);
-  LPA_CUDA(launch_fill_u64(counts, 0ull, 32, s));
-  LPA_CUDA(launch_fill_u64(counts + kNumClasses, 1ull, 1, s));  // profile: all integral
-  LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, counts, nullptr, nullptr, nullptr, nullptr,
-                           false, s));
-  LPA_CUDA(launch_weight_profile(p->off, p->w, n, p->m, counts + kNumClasses, s));
-  LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 32,
+  const int32_t nwin = (int32_t)num_windows(n);
+  int4* desc = (int4*)(p->ws + ly.desc);
+  int32_t* wtab = (int32_t*)(p->ws + ly.wtab);
+  int32_t* hcnt = (int32_t*)(p->ws + ly.hcnt);
+  int32_t* lcnt = (int32_t*)(p->ws + ly.lcnt);
+  int64_t* hub_prefix = (int64_t*)(p->ws + ly.hub_prefix);
+  int64_t* lane_prefix = (int64_t*)(p->ws + ly.lane_prefix);
+  unsigned long long* counts = (unsigned long long*)(p->ws + ly.counts);
+  // counts: [0, 3) weight profile
+  LPA_CUDA(launch_fill_u64(counts, 0ull, 8, s));
+  LPA_CUDA(launch_fill_u64(counts, 1ull, 1, s));  // profile: all integral until shown otherwise
+  LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, desc, wtab, hcnt, lcnt, s));
+  LPA_CUDA(launch_scan_counts(hcnt, nwin, hub_prefix, s));
+  LPA_CUDA(launch_scan_counts(lcnt, nwin, lane_prefix, s));
+  LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, (int4*)wp.hub_desc,
+                               ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
+  LPA_CUDA(launch_weight_profile(p->off, p->w, n, p->m, counts, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 3,
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 3, hub_prefix + nwin, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 4, lane_prefix + nwin, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
+  const double dmax = (double)p->host_cls[2];
+  if (dmax > 2147483647.0) return fail(LPA_EUNSUPPORTED, "a row has more than 2^31 - 1 entries");
   {
-    const bool integral = p->host_cls[kNumClasses] != 0;
-    unsigned bits = (unsigned)p->host_cls[kNumClasses + 1];
+    const bool integral = p->host_cls[0] != 0;
+    unsigned bits = (unsigned)p->host_cls[1];
     float wmax;
     memcpy(&wmax, &bits, sizeof(wmax));
-    const double dmax = (double)p->host_cls[kNumClasses + 2];
     p->exact_sums = integral && (double)wmax * dmax <= 16777216.0;
   }
-  int64_t acc = 0;
-  int64_t warps = 0;
-  for (int c = 0; c < kNumClasses; ++c) {
-    wp.cls_start[c] = acc;
-    acc += (int64_t)p->host_cls[c];
-  }
-  wp.cls_start[kNumClasses] = acc;
-  if (acc > n) return fail(LPA_EINTERNAL, "class binning counted %lld vertices", (long long)acc);
-  for (int c = 0; c < kMidClasses; ++c) {
-    wp.cls_warp_start[c] = (int32_t)warps;
-    const int L = 32 >> (c / kMidSub);
-    const int64_t cnt = (int64_t)p->host_cls[c];
-    warps += (cnt * L + 31) / 32;
-  }
-  wp.cls_warp_start[kMidClasses] = (int32_t)warps;
-  wp.nhubs = (int32_t)p->host_cls[kHubClass];
-  wp.mid_ctas = (int32_t)((warps + (kThreads / 32) - 1) / (kThreads / 32));
-  for (int c = 0; c < kNumClasses; ++c) p->host_cls[c] = (unsigned long long)wp.cls_start[c];
-  LPA_CUDA(cudaMemcpyAsync(cursors, p->host_cls, sizeof(unsigned long long) * kNumClasses,
-                           cudaMemcpyHostToDevice, s));
-  LPA_CUDA(launch_classify(p->off, n, p->e0, p->lmax, nullptr, (int32_t*)wp.perm_low,
-                           (int32_t*)wp.cnt_low, (int32_t*)wp.cls_list, cursors, true, s));
-  // low rows: one descriptor per sorted window slot
-  int4* desc = (int4*)(p->ws + p->lay.low_desc);
-  LPA_CUDA(launch_low_desc(p->off, wp.perm_low, wp.cnt_low, wp.nwin, desc, s));
-  wp.low_desc = desc;
-  wp.low_ctas = (int32_t)((int64_t)wp.nwin * (kWinVerts / kThreads));
-  const int64_t grid = (int64_t)wp.nhubs + wp.mid_ctas + wp.low_ctas;
-  if (grid > 0x7fffffffLL)
-    return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
-  p->nhubs = wp.nhubs;
-  p->nchunks = (int64_t)wp.mid_ctas + wp.low_ctas;
+  const int64_t nhubs = (int64_t)p->host_cls[3], nlanes = (int64_t)p->host_cls[4];
+  if (nhubs < 0 || nhubs > ly.hub_cap || nlanes < 0 || nlanes > ly.lane_cap)
+    return fail(LPA_EINTERNAL, "window binning counted %lld hubs and %lld lanes", (long long)nhubs,
+                (long long)nlanes);
+  const int64_t nctas = nhubs + (nlanes + kThreads - 1) / kThreads;
+  if (nctas > 0x7fffffffLL) return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
+  wp.nhubs = (int32_t)nhubs;
+  wp.nlanes = nlanes;
+  wp.nctas = (int32_t)nctas;
+  p->nhubs = nhubs;
+  p->nchunks = nctas - nhubs;
   return LPA_OK;
 }
 
@@ -366,7 +396,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
 
   // workspace: fixed part now; exact-mode hub tables once binning knows their size
-  p->lay = layout(n, p->mode, p->mode == kExact ? 2 * m : 0);
+  p->lay = layout(n, m, p->mode, p->e0, p->mode == kExact ? 2 * m : 0);
   if (o.workspace) {
     if (o.workspace_bytes < p->lay.total)
       return bail(fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, p->lay.total));
@@ -419,6 +449,12 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   }
   s = p->mode == kExact ? bin_chunks(p, o) : bin_classes(p);
   if (s != LPA_OK) return bail(s);
+  if (p->mode != kExact && p->wp.nhubs > 0 && p->wp.nlanes > 0) {
+    ce = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "side stream: %s", cudaGetErrorString(ce)));
+  }
   if (p->flags & LPA_TIMING) {
     ce = cudaEventRecord(ev1, p->stream);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(ev1);
@@ -536,9 +572,16 @@ void lpa_options_init(lpa_options* opt) {
 }
 
 size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k) {
+  return lpa_workspace_size_ex(n, m, mode, k, nullptr);
+}
+
+size_t lpa_workspace_size_ex(int32_t n, int64_t m, lpa_mode mode, int32_t k,
+                             const lpa_options* opt) {
   (void)k;
   if (n < 0 || m < 0) return 0;
-  return layout(n, (int)mode, mode == LPA_EXACT ? 2 * m : 0).total;
+  const int e0 = opt ? opt->leaf_e0 : 64;
+  if (e0 < 1) return 0;
+  return layout(n, m, (int)mode, e0, mode == LPA_EXACT ? 2 * m : 0).total;
 }
 
 size_t lpa_modularity_workspace_size(int32_t n) {

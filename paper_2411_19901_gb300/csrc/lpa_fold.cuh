@@ -265,8 +265,9 @@ struct Feeder {
 // Fold positions [b, e) of the CSR, in order, into st: st.add(C[j], w) for every kept
 // position.  The range is read as aligned groups of four (16-byte index and weight
 // loads); only the first and last group carry a mask.  Software pipeline with three
-// register sets rotated by unrolling (no register moves): while group k is folded, the
-// labels of group k+1 are being gathered and group k+2 is being loaded.
+// register sets rotated by unrolling (no moves of registers with loads in flight): while
+// group k is folded, the labels of group k+1 are being gathered and group k+2 is being
+// loaded.
 template <class S, bool WT, bool SKIP_SELF, bool RUNS = false>
 __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ idx,
                                            const float* __restrict__ wts,
@@ -296,11 +297,16 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
     if (k == ng - 1) mk &= lastm;
     X = gather_group<SKIP_SELF>(lab, X, W, mk, self);
   };
-  auto fold = [&](const int4& C, const float4& W) {
-    fd.push(C.x, W.x);
-    fd.push(C.y, W.y);
-    fd.push(C.z, W.z);
-    fd.push(C.w, W.w);
+  // one push site per step: the group's four pairs are shifted through lane x (its
+  // registers hold finished gathers, so the moves wait on nothing), which keeps the
+  // loop body, and the sketch code inlined into it, small for the instruction cache
+  auto fold = [&](int4 C, float4 W) {
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+      fd.push(C.x, W.x);
+      C = make_int4(C.y, C.z, C.w, -1);
+      W = make_float4(W.y, W.z, W.w, 0.f);
+    }
   };
   int4 X0, X1 = make_int4(self, self, self, self), X2 = make_int4(self, self, self, self);
   float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -324,58 +330,38 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
 
 // ------------------------------------------------------------ work decomposition
 
-// Kernel work map over a binned graph: CTAs [0, nhubs) take one hub each; then
-// mid_ctas CTAs whose warps take 32/L vertices of one mid class (L lanes per vertex,
-// one leaf per lane); then low_ctas CTAs whose warps take 32 degree-sorted low rows of
-// one window (one row per lane).
+// Work map over a binned graph for kernels of kThreads-thread CTAs (modularity): CTA c <
+// nhubs takes hub c whole; the following CTAs take the packed lanes in order, one lane
+// descriptor per thread.
 struct Work {
-  int kind;    // 0 hub, 1 mid, 2 low, -1 none
+  int kind;    // 0 hub (the whole CTA), 1 a lane of a mid or low vertex
   int v;       // vertex (or -1 for an idle lane)
-  int leaf;    // leaf index of this lane (mid), 0 otherwise
-  int L;       // leaves of the vertex (mid: the class's L; low: 1)
-  int64_t b;   // row start and length (mid and low lanes with a vertex)
+  int leaf;    // leaf index of this lane, 0 for a hub
+  int L;       // leaves of the vertex (1 for low rows and idle lanes; hubs: unused)
+  int64_t b;   // hub: row start and length; lane: its leaf's start and length
   int64_t d;
 };
 
-__device__ __forceinline__ Work lane_work(const WarpPlan& p, const int64_t* __restrict__ off,
-                                          int cta, int warp, int lane) {
-  Work w{-1, -1, 0, 1, 0, 0};
+// The work of thread tid of CTA cta: a hub CTA, or one lane of the packed mid and low
+// vertices.
+__device__ __forceinline__ Work lane_work(const WarpPlan& p, int cta, int tid) {
+  Work w{1, -1, 0, 1, 0, 0};
   if (cta < p.nhubs) {
+    const int4 h = __ldg(p.hub_desc + cta);
     w.kind = 0;
-    w.v = p.cls_list[p.cls_start[kHubClass] + cta];
+    w.v = h.x;
+    w.b = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
+    w.d = h.w;
     return w;
   }
-  cta -= p.nhubs;
-  if (cta < p.mid_ctas) {
-    w.kind = 1;
-    const int gw = cta * (kThreads / 32) + warp;
-    if (gw >= p.cls_warp_start[kMidClasses]) return w;
-    int c = 0;
-    while (gw >= p.cls_warp_start[c + 1]) ++c;
-    const int L = 32 >> (c / kMidSub);
-    w.L = L;
-    const int64_t slot = (int64_t)(gw - p.cls_warp_start[c]) * (32 / L) + lane / L;
-    const int64_t cnt = p.cls_start[c + 1] - p.cls_start[c];
-    w.leaf = lane % L;
-    if (slot < cnt) {
-      w.v = p.cls_list[p.cls_start[c] + slot];
-      w.b = off[w.v];
-      w.d = off[w.v + 1] - w.b;
-    }
-    return w;
-  }
-  cta -= p.mid_ctas;
-  w.kind = 2;
-  const int lw = cta * (kThreads / 32) + warp;
-  const int win = lw / (kWinVerts / 32);
-  if (win >= p.nwin) return w;
-  const int pos = (lw % (kWinVerts / 32)) * 32 + lane;
-  if (pos < p.cnt_low[win]) {
-    const int4 dsc = __ldg(p.low_desc + (int64_t)win * kWinVerts + pos);
-    w.v = dsc.x;
-    w.b = (int64_t)(uint32_t)dsc.y | ((int64_t)dsc.z << 32);
-    w.d = dsc.w;
-  }
+  const int64_t q = (int64_t)(cta - p.nhubs) * kThreads + tid;
+  if (q >= p.nlanes) return w;
+  const int4 l = __ldg(p.lane_desc + q);
+  w.v = l.x;
+  w.b = (int64_t)(uint32_t)l.y | ((int64_t)l.z << 32);
+  w.d = l.w & ((1 << kLaneLeafShift) - 1);
+  w.leaf = (l.w >> kLaneLeafShift) & 31;
+  w.L = 1 << (l.w >> kLaneLgShift);
   return w;
 }
 

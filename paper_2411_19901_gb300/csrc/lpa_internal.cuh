@@ -1,15 +1,13 @@
 // lpa_internal.cuh -- definitions shared by the library's translation units.
 //
 // Work decomposition of one sweep (the move step of Alg. 1):
-//   * "chunks": runs of consecutive vertices whose rows together fit one CTA's
-//     shared-memory stage (cost <= kChunkCap, see binning below).  A CTA stages the
-//     chunk's (neighbour label, weight) pairs edge-parallel, then every thread folds
-//     one leaf (partial sketch, Sec. 4.3) from shared memory, and leaves of one vertex
-//     merge by warp shuffles.
-//   * "hubs": vertices whose row is longer than a chunk, or that have more than 32
-//     leaves.  One CTA per hub; each thread folds one leaf straight from global
-//     memory; leaves merge by shuffles within a warp and through shared memory across
-//     warps, always in the stride-doubling order, so results never depend on the path.
+//   * sketch modes (MG, BM): the window binning below.  Hubs take a CTA each (one leaf
+//     per thread; leaves merge by shuffles within a warp and through shared memory
+//     across warps); every other vertex takes L consecutive lanes of the lane kernel, one
+//     leaf (partial sketch, Sec. 4.3) per lane, merged by warp shuffles.  Merges always
+//     follow the stride-doubling order, so results never depend on the path.
+//   * exact mode: "chunks", runs of consecutive vertices whose rows together fit one
+//     CTA's shared-memory table (cost <= kChunkCapExact), and hubs with global tables.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,23 +18,43 @@
 namespace lpa {
 
 constexpr int kThreads = 256;          // threads per CTA; also max leaves per chunk
+constexpr int kLaneThreads = 128;      // threads per CTA of the lane sweep
 constexpr int kChunkCap = 4096;        // sketch modes: max chunk cost (>= its edges)
 constexpr int kChunkCapExact = 2048;   // exact mode: its smem table needs 2 slots/edge
 constexpr int kMaxWarpLeaves = 32;     // vertices with more leaves become hubs
 constexpr int kSegment = 2048;         // vertices per thread of the greedy binning
 constexpr int kMaxLeaves = 256;        // largest leaf_max accepted
 
-// Binning of the warp-per-row sweep (sketch modes).  Low rows (one leaf) are sorted by
-// degree inside windows of kWinVerts consecutive vertices; mid vertices (2..32 leaves)
-// fall into kMidClasses classes by leaf count and leaf length; hubs (rows longer than
-// kHubDegree or more than 32 leaves) get a CTA each.
+// Binning of the warp-per-row sweep (sketch modes).  Vertices are cut into windows of
+// kWinVerts consecutive ids.  Inside a window they are counting-sorted into hubs (rows
+// longer than kHubDegree or with more than 32 leaves), then kMidClasses mid classes
+// (2..32 leaves, by leaf count descending, then leaf-length quarter), then one-leaf (low)
+// rows by degree, descending.  Mid and low vertices are packed onto consecutive lanes, L
+// lanes for a vertex of L leaves: as L only decreases along the order and divides 32,
+// each vertex's lanes start at a multiple of L and stay inside one warp.  Each window's
+// lanes are padded to whole warps and the windows' lanes concatenated in id order, one
+// 16-byte descriptor per lane, so a thread finds its work with one load and rows swept at
+// the same time share neighbour-label ranges in L2.  The grid runs every hub first (a CTA
+// each), then the lanes, kThreads to a CTA.
 constexpr int kWinVerts = 4096;
-constexpr int kLowKeys = 1024;         // counting-sort keys (degree, capped)
+constexpr int kLowKeys = 1024;         // low-row sort keys (degree, capped)
 constexpr int kMidSub = 4;             // leaf-length quarters per leaf count
 constexpr int kMidClasses = 5 * kMidSub;
-constexpr int kHubClass = kMidClasses;
-constexpr int kNumClasses = kMidClasses + 1;
+constexpr int kLaneGroups = kMidClasses + 1;  // mid classes, then the low rows
+constexpr int kSortKeys = 1 + kMidClasses + kLowKeys;
 constexpr int kHubDegree = 4096;
+// Per-window table (kWinTab int32): [0] hub count; [kTabLane + g] first lane of lane group
+// g; [kTabLanes] lanes in use; [kTabVert + g] window slot of group g's first vertex.
+constexpr int kTabLane = 1;
+constexpr int kTabLanes = kTabLane + kLaneGroups;
+constexpr int kTabVert = 24;
+constexpr int kWinTab = 48;
+static_assert(kTabLanes < kTabVert && kTabVert + kLaneGroups <= kWinTab, "window table layout");
+// Lane descriptor word w: leaf length (< 2^13, rows of a lane have <= kHubDegree
+// positions), leaf index, log2 of the vertex's leaf count.
+constexpr int kLaneLeafShift = 13;
+constexpr int kLaneLgShift = 18;
+static_assert(kHubDegree < (1 << kLaneLeafShift), "leaf length field");
 constexpr int kDnSlots = 64;           // dN is spread over this many counters
 
 enum Mode { kExact = 0, kMG = 1, kBM = 2 };
@@ -75,16 +93,11 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
 
 // Binned graph as the warp-per-row kernels see it.
 struct WarpPlan {
-  const int32_t* perm_low;  // per window: low rows sorted by degree (descending)
-  const int32_t* cnt_low;   // low rows per window
-  const int4* low_desc;     // per window slot: {v, offset low, offset high, degree}
-  const int32_t* cls_list;  // mid classes then hubs
-  int64_t cls_start[kNumClasses + 1];
-  int32_t cls_warp_start[kMidClasses + 1];
-  int32_t nwin;
+  const int4* hub_desc;   // per hub: {v, offset lo, offset hi, degree}
+  const int4* lane_desc;  // per lane (see kLaneLeafShift); v = -1 on padding lanes
+  int64_t nlanes;         // a multiple of 32
   int32_t nhubs;
-  int32_t mid_ctas;
-  int32_t low_ctas;         // nwin * kWinVerts / kThreads
+  int32_t nctas;          // nhubs + ceil(nlanes / kThreads)
 };
 
 // Arguments of one sweep launch.
@@ -130,12 +143,13 @@ struct BinArgs {
 // Host-side launchers (stream-ordered, no synchronisation).
 // Sketch modes (MG, BM): warp-per-row kernel over a WarpPlan.
 // runs: fold runs of equal labels as one add (MG; only when row sums are exact in fp32).
+// The hub kernel goes to s_hub, the lane kernel to s.
 cudaError_t launch_sweep_warp(int mode, int k, bool weighted, bool runs, const SweepArgs& a,
-                              const WarpPlan& p, cudaStream_t s);
+                              const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
 cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaStream_t s_hub);
 cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaStream_t s_hub);
 // Weight profile: out[0] = 1 if every weight is integer-valued (AND), out[1] = largest
 // weight's bits, out[2] = largest row length.  out must be zeroed except out[0] = 1.
 cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
@@ -143,20 +157,25 @@ cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n,
 // Exact mode: chunk kernel over the chunk/hub binning.
 cudaError_t launch_sweep_exact(bool weighted, const SweepArgs& a, cudaStream_t s);
 size_t exact_smem_bytes(bool weighted);
-// Binning for the warp-per-row kernels: counts per class, then the lists.
-cudaError_t launch_classify(const int64_t* off, int32_t n, int e0, int lmax,
-                            unsigned long long* counts, int32_t* perm_low, int32_t* cnt_low,
-                            int32_t* cls_list, unsigned long long* cursors, bool fill,
-                            cudaStream_t s);
+// Binning for the warp-per-row kernels.  Per window: sort the vertices into groups, write
+// their descriptors, the window table, the hub count and the padded lane count.
+cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int4* desc,
+                               int32_t* wtab, int32_t* hcnt, int32_t* lcnt, cudaStream_t s);
+// prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s);
+// Hub and lane descriptors of every window at their prefix offsets (capacities bound the
+// writes).
+cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
+                                const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
+                                int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
+                                cudaStream_t s);
 // Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.
 cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const float* w,
                                    int64_t m, const int32_t* labels, int32_t n,
                                    const WarpPlan& p, double* sigma_c, double* partials,
                                    int64_t npart, double* out4, cudaStream_t s);
 int64_t modularity_plan_partials(const WarpPlan& p, int32_t n);
-// Low-row descriptors {v, offset, degree} for every sorted window slot.
-cudaError_t launch_low_desc(const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low,
-                            int32_t nwin, int4* desc, cudaStream_t s);
+
 cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* out,
                           cudaStream_t s);
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w,

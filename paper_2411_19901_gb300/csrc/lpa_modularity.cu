@@ -14,22 +14,38 @@ namespace {
 constexpr int kModSlots = 4096;
 constexpr int kSqBlocks = 152 * 8;
 
-// Row accumulator driven by fold_range: add(C[j], w) for every entry with w > 0.
+// Row accumulator driven by fold_range: add(C[j], w) for every entry with w > 0.  Both
+// sums (K_i and the intra-community weight) are kept as unevaluated fp32 pairs hi + lo
+// updated by Knuth's TwoSum, which is exact: each pair holds its running sum to about
+// 2^-48 relative, so a leaf's totals match an fp64 sum far inside the 1e-9 tolerance
+// while every per-entry operation stays on the fp32 pipe (fp64 runs at a small fraction
+// of its rate on this GPU).  The leaf totals continue in fp64.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float w) {
+  const float s = hi + w;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (w - bb);
+  hi = s;
+  lo += err;
+}
+
 struct ModAcc {
-  double kv;
-  double in;
+  float kh, kl, ih, il;
   int cv;
   __device__ __forceinline__ void add(int c, float w) {
-    kv += (double)w;
-    in += (c == cv) ? (double)w : 0.0;
+    two_sum_add(kh, kl, w);
+    if (c == cv) two_sum_add(ih, il, w);
   }
+  __device__ __forceinline__ double k() const { return (double)kh + (double)kl; }
+  __device__ __forceinline__ double in() const { return (double)ih + (double)il; }
 };
 
-__device__ __forceinline__ double warp_down_sum(double x, int width_mask_lane, int L) {
-  (void)width_mask_lane;
-  for (int s = 1; s < L; s <<= 1) {
+// Sum over the L lanes of an aligned group into its first lane.  Lanes of one warp may
+// have different L (packed groups): all run the warp's largest L, adding only below their
+// own; lanes that are not group leaders end with partial sums that are never read.
+__device__ __forceinline__ double warp_down_sum(double x, int L, int Lw) {
+  for (int s = 1; s < Lw; s <<= 1) {
     const double y = __shfl_down_sync(kFullMask, x, s);
-    x += y;  // lanes that are not group leaders hold partial garbage, never read
+    if (s < L) x += y;
   }
   return x;
 }
@@ -41,21 +57,22 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
     double* sigma_c, double* slots) {
   __shared__ double s_k[kThreads], s_in[kThreads];
   const int tid = threadIdx.x, lane = tid & 31;
-  const Work wk = lane_work(p, off, (int)blockIdx.x, tid >> 5, lane);
-  ModAcc acc{0.0, 0.0, -1};
-  bool owner = false;  // this thread ends holding a vertex total
+  const Work wk = lane_work(p, (int)blockIdx.x, tid);
+  ModAcc acc{0.f, 0.f, 0.f, 0.f, -1};
+  double kv = 0.0, in = 0.0;  // this thread's totals
+  bool owner = false;         // this thread ends holding a vertex total
   int v = -1;
   if (wk.kind == 0) {
     v = wk.v;
-    const int64_t base = off[v];
-    const int64_t d = off[v + 1] - base;
+    const int64_t base = wk.b;
+    const int64_t d = wk.d;
     const int L = leaf_count(d, 1, kThreads);  // split the row over all threads
     acc.cv = labels[v];
     if (tid < L)
       fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (tid * d) / L,
                                     base + ((tid + 1) * d) / L);
-    s_k[tid] = acc.kv;
-    s_in[tid] = acc.in;
+    s_k[tid] = acc.k();
+    s_in[tid] = acc.in();
     __syncthreads();
     for (int s = kThreads / 2; s > 0; s >>= 1) {  // fixed-order tree
       if (tid < s) {
@@ -65,28 +82,30 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
       __syncthreads();
     }
     if (tid == 0) {
-      acc.kv = s_k[0];
-      acc.in = s_in[0];
+      kv = s_k[0];
+      in = s_in[0];
       owner = true;
     }
     __syncthreads();
-  } else if (wk.kind > 0) {
+  } else {
     v = wk.v;
     if (v >= 0) {
       acc.cv = labels[v];
-      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, wk.b + (wk.leaf * wk.d) / wk.L,
-                                    wk.b + ((wk.leaf + 1) * wk.d) / wk.L);
+      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, wk.b, wk.b + wk.d);
     }
-    if (wk.L > 1) {
-      acc.kv = warp_down_sum(acc.kv, 0, wk.L);
-      acc.in = warp_down_sum(acc.in, 0, wk.L);
+    kv = acc.k();
+    in = acc.in();
+    const int Lw = __reduce_max_sync(kFullMask, wk.L);
+    if (Lw > 1) {
+      kv = warp_down_sum(kv, wk.L, Lw);
+      in = warp_down_sum(in, wk.L, Lw);
     }
     owner = v >= 0 && wk.leaf == 0;
   }
   // Sigma_c: lanes of one warp with the same label add through their lowest lane
   const int key = owner ? acc.cv : -(lane + 2);
   const unsigned grp = __match_any_sync(kFullMask, key);
-  s_k[tid] = owner ? acc.kv : 0.0;
+  s_k[tid] = owner ? kv : 0.0;
   __syncwarp();
   if (owner && lane == __ffs(grp) - 1) {
     double sum = 0.0;
@@ -95,8 +114,8 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
   }
   __syncthreads();
   // block totals of K_i and of intra-community weight
-  s_k[tid] = owner ? acc.kv : 0.0;
-  s_in[tid] = owner ? acc.in : 0.0;
+  s_k[tid] = owner ? kv : 0.0;
+  s_in[tid] = owner ? in : 0.0;
   __syncthreads();
   for (int s = kThreads / 2; s > 0; s >>= 1) {
     if (tid < s) {
@@ -183,7 +202,7 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
   count_launch();
   zero_f64_kernel<<<16, 256, 0, s>>>(slots, 2 * kModSlots);
   count_launch();
-  const unsigned grid = (unsigned)(p.nhubs + p.mid_ctas + p.low_ctas);
+  const unsigned grid = (unsigned)p.nctas;
   if (grid > 0) {
     if (w)
       modularity_plan_kernel<true><<<grid, kThreads, 0, s>>>(off, idx, w, m, labels, p, sigma_c, slots);

@@ -177,118 +177,168 @@ __global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t
 
 // ------------------------------------------------- binning for the warp sweep
 
-// Class of a vertex with d positions: -1 low (one leaf; *key = capped degree for the
-// window sort), [0, kMidClasses) mid (2..32 leaves; larger L and longer leaves first),
-// kHubClass for rows longer than kHubDegree or with more than 32 leaves.
-__device__ __forceinline__ int vertex_class(int64_t d, int e0, int lmax, int* key) {
+// Sort key of a vertex with d positions inside its window: 0 hub; 1 + c for mid class c
+// (larger L and longer leaves first); 1 + kMidClasses + (kLowKeys - 1 - min(d, kLowKeys-1))
+// for a one-leaf row (longer rows first).
+__device__ __forceinline__ int window_key(int64_t d, int e0, int lmax) {
   const int L = leaf_count(d, e0, lmax);
-  if (d > kHubDegree || L > kMaxWarpLeaves) return kHubClass;
-  if (L == 1) {
-    *key = (int)(d < kLowKeys ? d : kLowKeys - 1);
-    return -1;
-  }
+  if (d > kHubDegree || L > kMaxWarpLeaves) return 0;
+  if (L == 1) return 1 + kMidClasses + (kLowKeys - 1 - (int)(d < kLowKeys ? d : kLowKeys - 1));
   const int lidx = 5 - (31 - __clz(L));  // L = 32 -> 0 ... L = 2 -> 4
   int sub = (int)(((d / L) * 4) / e0) - 4;  // leaf length quarter in [e0, 2 e0)
   sub = sub < 0 ? 0 : (sub > kMidSub - 1 ? kMidSub - 1 : sub);
-  return lidx * kMidSub + (kMidSub - 1 - sub);
+  return 1 + lidx * kMidSub + (kMidSub - 1 - sub);
 }
 
-constexpr int kClassifyThreads = 1024;
+constexpr int kSortThreads = 1024;
+constexpr int kSortPad = 2 * kSortThreads;  // scan space: two keys per thread
+static_assert(kSortKeys <= kSortPad, "sort keys exceed the scan space");
 
-__global__ void __launch_bounds__(kClassifyThreads) classify_count_kernel(
-    const int64_t* off, int32_t n, int e0, int lmax, unsigned long long* counts) {
-  __shared__ unsigned int s_cnt[kNumClasses];
-  if (threadIdx.x < kNumClasses) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t v0 = (int64_t)blockIdx.x * kWinVerts;
-  for (int i = threadIdx.x; i < kWinVerts; i += kClassifyThreads) {
-    const int64_t v = v0 + i;
-    if (v >= n) break;
-    int key;
-    const int c = vertex_class(off[v + 1] - off[v], e0, lmax, &key);
-    if (c >= 0) atomicAdd(&s_cnt[c], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x < kNumClasses && s_cnt[threadIdx.x])
-    atomicAdd(counts + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
-}
-
-// One CTA per window: low rows are counting-sorted by degree (descending) into the
-// window's slice of perm_low; mid and hub vertices are appended to their class lists
-// (cursors start at each class's offset).  Order inside a key or class does not matter.
-__global__ void __launch_bounds__(kClassifyThreads) classify_fill_kernel(
-    const int64_t* off, int32_t n, int e0, int lmax, int32_t* perm_low, int32_t* cnt_low,
-    int32_t* cls_list, unsigned long long* cursors) {
-  __shared__ int s_hist[kLowKeys];
-  __shared__ unsigned int s_cnt[kNumClasses];
-  __shared__ unsigned long long s_base[kNumClasses];
-  __shared__ int s_wsum[kClassifyThreads / 32];
-  constexpr int kPer = kWinVerts / kClassifyThreads;
+// One CTA per window: counting sort of the window's vertices by window_key, writing each
+// slot's descriptor {v, offset lo, offset hi, degree}, the window table, the window's hub
+// count and its lane count rounded up to whole warps.  Order inside one key does not
+// matter.
+__global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
+    const int64_t* off, int32_t n, int e0, int lmax, int4* desc, int32_t* wtab, int32_t* hcnt,
+    int32_t* lcnt) {
+  __shared__ int s_hist[kSortPad];
+  __shared__ int s_wsum[kSortThreads / 32];
+  __shared__ int s_grp[1 + kLaneGroups];  // hubs, mid classes, low rows
+  constexpr int kPer = kWinVerts / kSortThreads;
   const int tid = threadIdx.x;
-  for (int i = tid; i < kLowKeys; i += kClassifyThreads) s_hist[i] = 0;
-  if (tid < kNumClasses) s_cnt[tid] = 0;
+  for (int i = tid; i < kSortPad; i += kSortThreads) s_hist[i] = 0;
   __syncthreads();
   const int64_t v0 = (int64_t)blockIdx.x * kWinVerts;
-  int cls[kPer], key[kPer];
+  int key[kPer];
+  int64_t b[kPer];
+  int d[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    const int64_t v = v0 + tid + q * kClassifyThreads;
-    cls[q] = -2;
-    key[q] = 0;
+    const int64_t v = v0 + tid + q * kSortThreads;
+    key[q] = -1;
     if (v < n) {
-      cls[q] = vertex_class(off[v + 1] - off[v], e0, lmax, &key[q]);
-      if (cls[q] == -1)
-        atomicAdd(&s_hist[key[q]], 1);
-      else
-        atomicAdd(&s_cnt[cls[q]], 1u);
+      b[q] = off[v];
+      const int64_t dd = off[v + 1] - b[q];
+      d[q] = (int)dd;  // rows above INT32_MAX are refused after binning
+      key[q] = window_key(dd, e0, lmax);
+      atomicAdd(&s_hist[key[q]], 1);
     }
   }
   __syncthreads();
-  // exclusive scan of the histogram in descending key order: thread t owns key K-1-t
-  const int k = kLowKeys - 1 - tid;
-  const int x = (tid < kLowKeys) ? s_hist[k] : 0;
-  int incl = x;
+  if (tid <= kLaneGroups) {
+    int c = 0;
+    if (tid <= kMidClasses) {
+      c = s_hist[tid];
+    } else {
+      for (int k = 1 + kMidClasses; k < kSortKeys; ++k) c += s_hist[k];
+    }
+    s_grp[tid] = c;
+  }
+  // exclusive scan of the histogram, keys 2t and 2t+1 owned by thread t
+  const int x0 = s_hist[2 * tid], x1 = s_hist[2 * tid + 1];
+  int incl = x0 + x1;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, incl, o);
     if ((tid & 31) >= o) incl += y;
   }
   if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
-  if (tid < kNumClasses) s_base[tid] = s_cnt[tid] ? atomicAdd(cursors + tid, (unsigned long long)s_cnt[tid]) : 0;
   __syncthreads();
   int wpre = 0;
   for (int w = 0; w < (tid >> 5); ++w) wpre += s_wsum[w];
-  if (tid < kLowKeys) s_hist[k] = wpre + incl - x;  // becomes the key's cursor
-  if (tid == kClassifyThreads - 1) {
-    int tot = 0;
-    for (int w = 0; w < kClassifyThreads / 32; ++w) tot += s_wsum[w];
-    cnt_low[blockIdx.x] = tot;
+  const int ex = wpre + incl - x0 - x1;
+  s_hist[2 * tid] = ex;
+  s_hist[2 * tid + 1] = ex + x0;
+  if (tid == 0) {
+    int32_t* t = wtab + (int64_t)blockIdx.x * kWinTab;
+    const int nh = s_grp[0];
+    int lanes = 0, slot = nh;
+    for (int g = 0; g < kLaneGroups; ++g) {
+      t[kTabLane + g] = lanes;
+      t[kTabVert + g] = slot;
+      const int cnt = s_grp[1 + g];
+      lanes += cnt * (g < kMidClasses ? 32 >> (g / kMidSub) : 1);
+      slot += cnt;
+    }
+    t[0] = nh;
+    t[kTabLanes] = lanes;
+    hcnt[blockIdx.x] = nh;
+    lcnt[blockIdx.x] = (lanes + 31) & ~31;
   }
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    const int64_t v = v0 + tid + q * kClassifyThreads;
-    if (cls[q] == -1) {
-      const int pos = atomicAdd(&s_hist[key[q]], 1);
-      perm_low[v0 + pos] = (int32_t)v;
-    } else if (cls[q] >= 0) {
-      const unsigned long long pos = atomicAdd(&s_base[cls[q]], 1ull);
-      cls_list[pos] = (int32_t)v;
-    }
+    if (key[q] < 0) continue;
+    const int64_t v = v0 + tid + q * kSortThreads;
+    const int pos = atomicAdd(&s_hist[key[q]], 1);
+    desc[v0 + pos] = make_int4((int)v, (int)(uint32_t)(b[q] & 0xffffffffLL), (int)(b[q] >> 32), d[q]);
   }
 }
 
-// Low-row descriptors: each sorted window slot's {v, offset (two halves), degree}, so a
-// sweep lane reads its row with one 16-byte load.
-__global__ void __launch_bounds__(kClassifyThreads) low_desc_kernel(
-    const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low, int4* desc) {
-  const int win = blockIdx.x;
-  const int cnt = cnt_low[win];
-  int4* d = desc + (int64_t)win * kWinVerts;
-  for (int pos = threadIdx.x; pos < cnt; pos += kClassifyThreads) {
-    const int v = perm_low[(int64_t)win * kWinVerts + pos];
-    const int64_t b = off[v];
-    d[pos] = make_int4(v, (int)(uint32_t)(b & 0xffffffffLL), (int)(b >> 32), (int)(off[v + 1] - b));
+// Exclusive prefix sum of len int32 counts into int64 prefix[0, len]; prefix[len] = total.
+__global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(const int32_t* cnt, int64_t len,
+                                                                   int64_t* prefix) {
+  __shared__ int64_t sv[kScanThreads];
+  const int tid = threadIdx.x;
+  const int64_t per = (len + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = min(len, tid * per), hi = min(len, lo + per);
+  int64_t t = 0;
+  for (int64_t i = lo; i < hi; ++i) t += cnt[i];
+  sv[tid] = t;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
+    const int64_t x = tid >= o ? sv[tid - o] : 0;
+    __syncthreads();
+    sv[tid] += x;
+    __syncthreads();
+  }
+  int64_t r = sv[tid] - t;
+  for (int64_t i = lo; i < hi; ++i) {
+    prefix[i] = r;
+    r += cnt[i];
+  }
+  if (tid == kScanThreads - 1) prefix[len] = sv[tid];
+}
+
+// One CTA per window: copy the window's hub descriptors to hub_desc[hub_prefix[w] + i]
+// and write one lane descriptor per packed lane to lane_desc[lane_prefix[w] + q]:
+// {v, leaf start lo, leaf start hi, leaf length | leaf << kLaneLeafShift | log2 L <<
+// kLaneLgShift}, v = -1 for the padding lanes.  Writes past the capacities are skipped
+// (the host then refuses the plan).
+__global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
+    const int4* desc, const int32_t* wtab, const int64_t* hub_prefix, const int64_t* lane_prefix,
+    int4* hub_desc, int64_t hub_cap, int4* lane_desc, int64_t lane_cap) {
+  __shared__ int32_t t[kWinTab];
+  const int tid = threadIdx.x;
+  const int64_t win = blockIdx.x;
+  if (tid < kWinTab) t[tid] = wtab[win * kWinTab + tid];
+  __syncthreads();
+  const int4* wd = desc + win * kWinVerts;
+  const int nh = t[0];
+  const int64_t h0 = hub_prefix[win];
+  for (int i = tid; i < nh; i += kSortThreads)
+    if (h0 + i < hub_cap) hub_desc[h0 + i] = wd[i];
+  const int lanes = t[kTabLanes];
+  const int64_t l0 = lane_prefix[win];
+  const int padded = (int)(lane_prefix[win + 1] - l0);
+  for (int q = tid; q < padded; q += kSortThreads) {
+    if (l0 + q >= lane_cap) break;
+    int4 out = make_int4(-1, 0, 0, 0);
+    if (q < lanes) {
+      int g = 0;  // last lane group whose first lane is <= q (first lanes ascend)
+      for (int h = 16; h > 0; h >>= 1)
+        if (g + h < kLaneGroups && t[kTabLane + g + h] <= q) g += h;
+      const int lg = g < kMidClasses ? 5 - g / kMidSub : 0;
+      const int r = q - t[kTabLane + g];
+      const int L = 1 << lg, leaf = r & (L - 1);
+      const int4 dv = wd[t[kTabVert + g] + (r >> lg)];
+      const int64_t b = (int64_t)(uint32_t)dv.y | ((int64_t)dv.z << 32);
+      const int64_t d = dv.w;
+      const int64_t lo = b + (leaf * d) / L, hi = b + ((leaf + 1) * d) / L;
+      out = make_int4(dv.x, (int)(uint32_t)(lo & 0xffffffffLL), (int)(lo >> 32),
+                      (int)(hi - lo) | (leaf << kLaneLeafShift) | (lg << kLaneLgShift));
+    }
+    lane_desc[l0 + q] = out;
   }
 }
 
@@ -564,32 +614,35 @@ cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* o
   return cudaGetLastError();
 }
 
-cudaError_t launch_classify(const int64_t* off, int32_t n, int e0, int lmax,
-                            unsigned long long* counts, int32_t* perm_low, int32_t* cnt_low,
-                            int32_t* cls_list, unsigned long long* cursors, bool fill,
-                            cudaStream_t s) {
-  const unsigned nwin = (unsigned)((n + kWinVerts - 1) / kWinVerts);
-  if (nwin == 0) return cudaSuccess;
-  if (!fill)
-    classify_count_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, n, e0, lmax, counts);
-  else
-    classify_fill_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, n, e0, lmax, perm_low, cnt_low,
-                                                           cls_list, cursors);
-  count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_low_desc(const int64_t* off, const int32_t* perm_low, const int32_t* cnt_low,
-                            int32_t nwin, int4* desc, cudaStream_t s) {
-  if (nwin == 0) return cudaSuccess;
-  low_desc_kernel<<<nwin, kClassifyThreads, 0, s>>>(off, perm_low, cnt_low, desc);
-  count_launch();
-  return cudaGetLastError();
-}
-
 cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
                                   unsigned long long* out, cudaStream_t s) {
   weight_profile_kernel<<<grid_for(m > n ? m : n, 256), 256, 0, s>>>(off, w, n, m, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int4* desc,
+                               int32_t* wtab, int32_t* hcnt, int32_t* lcnt, cudaStream_t s) {
+  const unsigned nwin = (unsigned)((n + kWinVerts - 1) / kWinVerts);
+  if (nwin == 0) return cudaSuccess;
+  window_sort_kernel<<<nwin, kSortThreads, 0, s>>>(off, n, e0, lmax, desc, wtab, hcnt, lcnt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s) {
+  scan_counts_kernel<<<1, kScanThreads, 0, s>>>(cnt, len, prefix);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
+                                const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
+                                int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
+                                cudaStream_t s) {
+  if (nwin == 0) return cudaSuccess;
+  expand_lanes_kernel<<<(unsigned)nwin, kSortThreads, 0, s>>>(desc, wtab, hub_prefix, lane_prefix,
+                                                              hub_desc, hub_cap, lane_desc, lane_cap);
   count_launch();
   return cudaGetLastError();
 }

@@ -8,8 +8,10 @@
 //    step and no CTA barrier waits on a straggler;
 //  * mid rows (2..32 leaves): each lane folds one leaf; the L lanes of a vertex merge by
 //    the stride-doubling tree with warp shuffles (Sec. 4.3, partial sketches merged);
+//    mid and low vertices are packed lane by lane, so one warp may hold several L;
 //  * hubs (longer rows, or more than 32 leaves): one CTA, one leaf per thread, shuffles
-//    within warps, shared memory across warps.
+//    within warps, shared memory across warps (a kernel of their own, so the lane kernel
+//    runs CTAs of single warps that retire independently).
 // Every lane reads its range with the pipelined fold of lpa_fold.cuh (16-byte index and
 // weight loads two groups ahead, label gathers one group ahead).  The tree depends only
 // on the row length, so results never depend on which of these paths a vertex takes.
@@ -44,81 +46,107 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
   }
 }
 
-// RUNS folds runs of equal consecutive labels as one add (MG only; the caller enables it
-// when every sum of a row's weights is exact in fp32, so the bits do not change).
+// Hub sweep: CTA c sweeps hub c, one leaf per thread, leaves merged by shuffles within
+// warps and through shared memory across warps.  RUNS folds runs of equal consecutive
+// labels as one add (MG only; the caller enables it when every sum of a row's weights is
+// exact in fp32, so the bits do not change).
 template <class S, bool WT, bool RUNS>
-__global__ void __launch_bounds__(kThreads) sweep_warp_kernel(SweepArgs a, WarpPlan p) {
+__global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPlan p) {
   constexpr bool kRuns = RUNS && S::kRunMergeable;
   if (a.done != nullptr && *a.done) return;
   __shared__ int sk[(kThreads / 32) * 32];
   __shared__ float sv[(kThreads / 32) * 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int cta = (int)blockIdx.x;
-  int changed = 0;
-  if (cta < p.nhubs) {  // hub: the whole CTA, one leaf per thread
-    const int v = p.cls_list[p.cls_start[kHubClass] + cta];
-    const int64_t base = a.off[v];
-    const int64_t d = a.off[v + 1] - base;
-    const int L = leaf_count(d, a.e0, a.lmax);
-    const int own = a.c_prev[v];
-    S st;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int4 h = __ldg(p.hub_desc + blockIdx.x);
+  const int v = h.x;
+  const int64_t base = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
+  const int64_t d = h.w;
+  const int L = leaf_count(d, a.e0, a.lmax);
+  const int own = a.c_prev[v];
+  S st;
+  st.init(own);
+  if (tid < L)
+    fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
+                                   base + ((tid + 1) * d) / L);
+  const int Lw = L < 32 ? L : 32;
+  for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
+  if (L > 32) cross_warp_tree<S>(st, L, tid, sk, sv);
+  if (tid == 0) {
+    const int nl = commit_label(st.choose(), own, a.pick_less);
+    a.c_next[v] = nl;
+    if (nl != own) atomicAdd(a.dn + (blockIdx.x & (kDnSlots - 1)), 1ull);
+  }
+}
+
+// Lane sweep: thread q of the grid takes lane descriptor q (a low row, or one leaf of a
+// mid vertex whose L lanes are aligned inside the warp).  Lanes of one warp may belong to
+// vertices of different L: every lane runs the warp's largest L, merging only below its
+// own.  Warps are independent, so a CTA of kLaneThreads holds as few of them as possible.
+template <class S, bool WT, bool RUNS>
+__global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
+  constexpr bool kRuns = RUNS && S::kRunMergeable;
+  if (a.done != nullptr && *a.done) return;
+  const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int v = -1, leaf = 0, L = 1;
+  int64_t lo = 0, len = 0;
+  if (q < p.nlanes) {
+    const int4 l = __ldg(p.lane_desc + q);
+    v = l.x;
+    lo = (int64_t)(uint32_t)l.y | ((int64_t)l.z << 32);
+    len = l.w & ((1 << kLaneLeafShift) - 1);
+    leaf = (l.w >> kLaneLeafShift) & 31;
+    L = 1 << (l.w >> kLaneLgShift);
+  }
+  S st;
+  int own = -1;
+  if (v >= 0) {
+    own = a.c_prev[v];
     st.init(own);
-    if (tid < L)
-      fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
-                                     base + ((tid + 1) * d) / L);
-    const int Lw = L < 32 ? L : 32;
-    for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
-    if (L > 32) cross_warp_tree<S>(st, L, tid, sk, sv);
-    if (tid == 0) {
-      const int nl = commit_label(st.choose(), own, a.pick_less);
-      a.c_next[v] = nl;
-      changed = nl != own;
-    }
-  } else {  // mid leaf group or low row: one lane per leaf
-    const Work wk = lane_work(p, a.off, cta, warp, lane);
-    S st;
-    int own = -1;
-    if (wk.v >= 0) {
-      own = a.c_prev[wk.v];
-      st.init(own);
-      fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, wk.v,
-                                     wk.b + (wk.leaf * wk.d) / wk.L,
-                                     wk.b + ((wk.leaf + 1) * wk.d) / wk.L);
-    } else {
-      st.init(-1);
-    }
-    for (int s = 1; s < wk.L; s <<= 1) st.shfl_merge(s, wk.v >= 0 && (wk.leaf & (2 * s - 1)) == 0);
-    if (wk.v >= 0 && wk.leaf == 0) {
-      const int nl = commit_label(st.choose(), own, a.pick_less);
-      a.c_next[wk.v] = nl;
-      changed = nl != own;
-    }
+    fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
+  } else {
+    st.init(-1);
+  }
+  const int Lw = __reduce_max_sync(kFullMask, L);
+  for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, v >= 0 && s < L && (leaf & (2 * s - 1)) == 0);
+  int changed = 0;
+  if (v >= 0 && leaf == 0) {
+    const int nl = commit_label(st.choose(), own, a.pick_less);
+    a.c_next[v] = nl;
+    changed = nl != own;
   }
   const int wsum = __reduce_add_sync(kFullMask, changed);
   if (lane == 0 && wsum > 0)
-    atomicAdd(a.dn + ((blockIdx.x * (kThreads / 32) + warp) & (kDnSlots - 1)), (unsigned long long)wsum);
+    atomicAdd(a.dn + ((q >> 5) & (kDnSlots - 1)), (unsigned long long)wsum);
 }
 
-inline unsigned sweep_grid(const WarpPlan& p) {
-  return (unsigned)(p.nhubs + p.mid_ctas + p.low_ctas);
-}
-
+// One sweep: the hub kernel on s_hub and the lane kernel on s (the caller orders the two
+// streams; they may be the same stream).  Both write disjoint entries of c_next and add to
+// the same dN counters.
 template <class S, bool WT, bool RUNS>
-cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s) {
-  const unsigned grid = sweep_grid(p);
-  if (grid == 0) return cudaSuccess;
-  sweep_warp_kernel<S, WT, RUNS><<<grid, kThreads, 0, s>>>(a, p);
-  count_launch();
+cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                               cudaStream_t s_hub) {
+  if (p.nhubs > 0) {
+    sweep_hub_kernel<S, WT, RUNS><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
+    count_launch();
+  }
+  const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
+  if (lane_ctas > 0) {
+    sweep_lane_kernel<S, WT, RUNS><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 
 // The four instantiations of one sketch type: weighted or not, runs folded or not.
 template <class S>
 cudaError_t launch_warp_variants(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, cudaStream_t s_hub) {
   if (weighted)
-    return runs ? launch_warp_kernel<S, true, true>(a, p, s) : launch_warp_kernel<S, true, false>(a, p, s);
-  return runs ? launch_warp_kernel<S, false, true>(a, p, s) : launch_warp_kernel<S, false, false>(a, p, s);
+    return runs ? launch_warp_kernel<S, true, true>(a, p, s, s_hub)
+                : launch_warp_kernel<S, true, false>(a, p, s, s_hub);
+  return runs ? launch_warp_kernel<S, false, true>(a, p, s, s_hub)
+              : launch_warp_kernel<S, false, false>(a, p, s, s_hub);
 }
 
 }  // namespace lpa

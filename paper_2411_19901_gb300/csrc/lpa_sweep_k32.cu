@@ -4,8 +4,8 @@
 namespace lpa {
 
 cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
-                              cudaStream_t s) {
-  return launch_warp_variants<MGSketch<32>>(weighted, runs, a, p, s);
+                              cudaStream_t s, cudaStream_t s_hub) {
+  return launch_warp_variants<MGSketch<32>>(weighted, runs, a, p, s, s_hub);
 }
 
 }  // namespace lpa

@@ -100,6 +100,8 @@ _SIG = {
                                          _P]),
     "lpa_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                              ctypes.c_int32]),
+    "lpa_workspace_size_ex": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
+                                                ctypes.c_int32, _P]),
     "lpa_modularity_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
     "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
@@ -250,6 +252,12 @@ def lpa_modularity_noalloc(offsets, indices, weights, n, m, labels,
 
 def lpa_workspace_size(n, m, mode, k=8) -> int:
     return int(load().lpa_workspace_size(n, m, _mode(mode), k))
+
+
+def lpa_workspace_size_ex(n, m, mode, k=8, opt=None) -> int:
+    """Workspace bound for the given options (their leaf_e0 sets the lane table's size)."""
+    return int(load().lpa_workspace_size_ex(n, m, _mode(mode), k,
+                                            ctypes.byref(opt) if opt is not None else None))
 
 
 def lpa_modularity_workspace_size(n) -> int:

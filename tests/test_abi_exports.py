@@ -48,5 +48,12 @@ def test_host_only_calls():
     assert (o.pl_period, o.leaf_e0, o.leaf_max, o.flags) == (8, 64, 256, lpa.LPA_VALIDATE)
     assert lpa.lpa_workspace_size(1000, 10000, "mg") > 4 * 1000
     assert lpa.lpa_workspace_size(1000, 10000, "exact") > lpa.lpa_workspace_size(1000, 10000, "mg")
+    # the default options give the plain bound; a smaller leaf_e0 needs a larger lane table
+    assert lpa.lpa_workspace_size_ex(1000, 10000, "mg", 8, o) == lpa.lpa_workspace_size(1000, 10000, "mg")
+    o1 = lpa.lpa_options_init()
+    o1.leaf_e0 = 1
+    assert lpa.lpa_workspace_size_ex(1000, 10000, "mg", 8, o1) > lpa.lpa_workspace_size(1000, 10000, "mg")
+    o1.leaf_e0 = 0
+    assert lpa.lpa_workspace_size_ex(1000, 10000, "mg", 8, o1) == 0
     assert lpa.load().lpa_status_string(-1) == b"invalid argument"
     assert lpa.lpa_version().startswith("lpa-gb300")

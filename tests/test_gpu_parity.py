@@ -255,6 +255,15 @@ def test_workspace_stream_warm_start_and_host_entry(lpa):
         s.synchronize()
         r = oracle.lpa(g.offsets, g.indices, g.weights, mode=OMODE[mode])
         assert np.array_equal(labels.cpu().numpy(), r["labels"]), mode
+    # a smaller leaf_e0 needs the options-aware bound; the plain bound is refused
+    r1 = oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG, e0=1)
+    o1 = lpa.make_options(leaf_e0=1)
+    ws = torch.empty(lpa.lpa_workspace_size_ex(g.n, g.m, "mg", 8, o1), dtype=torch.uint8, device="cuda")
+    labels, st = lpa.detect(off, idx, w, mode="mg", leaf_e0=1, workspace=ws)
+    assert np.array_equal(labels.cpu().numpy(), r1["labels"])
+    small = torch.empty(lpa.lpa_workspace_size(g.n, g.m, "mg"), dtype=torch.uint8, device="cuda")
+    with pytest.raises(lpa.LpaError, match="workspace"):
+        lpa.detect(off, idx, w, mode="mg", leaf_e0=1, workspace=small)
     # warm start: one sweep from given labels, no pick-less
     lab = np.random.default_rng(3).integers(0, 100, g.n).astype(np.int32)
     labels, st = lpa.detect(off, idx, w, mode="mg", labels_in=torch.from_numpy(lab).cuda(),
