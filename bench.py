@@ -199,6 +199,20 @@ def share_graph(name: str, world: int, rank: int, barrier) -> tuple[synth.Graph,
     return g, time.perf_counter() - t0
 
 
+def aggregate_over_ranks(times_ms, counts, world: int, device):
+    """Whole-job figures: the max of each time and the sum of each count over ranks."""
+    if world == 1:
+        return [float(t) for t in times_ms], [float(c) for c in counts]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [float(x) for x in c.tolist()]
+
+
 def sweep_bytes(n: int, m: int, weighted: bool) -> int:
     """Algorithmic bytes of one sweep: per CSR entry its index, weight and the gathered
     neighbour label; per vertex its offset, old label and new label."""
@@ -357,17 +371,8 @@ def run_ours(args):
     barrier()
     e2e_edges = sum(s["iterations"] * m for s in e2e_stats)
 
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms, e2e_ms = float(t[0]), float(t[1])
-        tot = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        edges_all, e2e_edges_all = float(tot[0]), float(tot[1])
-    else:
-        edges_all, e2e_edges_all = float(edges), float(e2e_edges)
+    (elapsed_ms, e2e_ms), (edges_all, e2e_edges_all) = aggregate_over_ranks(
+        [elapsed_ms, e2e_ms], [edges, e2e_edges], world, dev)
 
     if rank != 0:
         if world > 1:

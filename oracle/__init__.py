@@ -24,6 +24,7 @@ _SRC = os.path.join(_HERE, "lpa_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 EXACT, MG, BM = 0, 1, 2
+PRUNE, UNCLAMPED, RESCAN = 1, 2, 4  # variant flags (pruning, paper-literal MG, double scan)
 
 _c_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _c_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
@@ -85,6 +86,24 @@ def _load():
         ctypes.c_void_p, _c_i32p, _c_i64p, ctypes.POINTER(ctypes.c_int32),
         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
     ]
+    lib.oracle_mg_sketch_ex.restype = ctypes.c_int
+    lib.oracle_mg_sketch_ex.argtypes = [
+        _c_i32p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_int32, ctypes.c_int32, _c_i32p, _c_f32p,
+    ]
+    lib.oracle_move_ex.restype = ctypes.c_int64
+    lib.oracle_move_ex.argtypes = [
+        ctypes.c_int32, _c_i64p, _c_i32p, ctypes.c_void_p, _c_i32p, _c_i32p, ctypes.c_void_p,
+        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+    ]
+    lib.oracle_lpa_ex.restype = ctypes.c_int
+    lib.oracle_lpa_ex.argtypes = [
+        ctypes.c_int32, _c_i64p, _c_i32p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+        ctypes.c_int32, ctypes.c_void_p, _c_i32p, _c_i64p, _c_i64p,
+        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+    ]
     lib.oracle_modularity.restype = ctypes.c_double
     lib.oracle_modularity.argtypes = [
         ctypes.c_int32, _c_i64p, _c_i32p, ctypes.c_void_p, _c_i32p,
@@ -115,14 +134,23 @@ def leaf_count(d: int, e0: int = 64, lmax: int = 256) -> int:
     return int(_load().oracle_leaf_count(d, e0, lmax))
 
 
-def mg_sketch(labels, weights=None, k: int = 8, e0: int = 64, lmax: int = 256):
-    """Final MG sketch (keys, vals) of a (label, weight) sequence; label < 0 = skip."""
+def mg_sketch(labels, weights=None, k: int = 8, e0: int = 64, lmax: int = 256,
+              unclamped: bool = False):
+    """Final MG sketch (keys, vals) of a (label, weight) sequence; label < 0 = skip.
+
+    The clamped sketch reports key -1 for empty slots; ``unclamped`` (the paper-literal
+    accumulate) returns the raw slots, whose values may be negative and whose empty slots
+    may keep a stale key."""
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
     keys = np.empty(k, dtype=np.int32)
     vals = np.empty(k, dtype=np.float32)
     lab_buf = lab if lab.size else np.zeros(1, dtype=np.int32)
-    rc = _load().oracle_mg_sketch(lab_buf, _wptr(w), lab.size, k, e0, lmax, keys, vals)
+    if unclamped:
+        rc = _load().oracle_mg_sketch_ex(lab_buf, _wptr(w), lab.size, k, e0, lmax, UNCLAMPED,
+                                         keys, vals)
+    else:
+        rc = _load().oracle_mg_sketch(lab_buf, _wptr(w), lab.size, k, e0, lmax, keys, vals)
     if rc != 0:
         raise ValueError("oracle_mg_sketch: bad arguments")
     return keys, vals
@@ -150,40 +178,61 @@ def choose(i, offsets, indices, weights, c_prev, mode=MG, k=8, e0=64, lmax=256) 
                                      e0, lmax))
 
 
+def _flags(prune=False, unclamped=False, rescan=False) -> int:
+    return (PRUNE if prune else 0) | (UNCLAMPED if unclamped else 0) | (RESCAN if rescan else 0)
+
+
 def move(offsets, indices, weights, c_prev, mode=MG, k=8, e0=64, lmax=256,
-         pick_less=False, threads=1):
-    """One synchronous sweep; returns (c_next, dN)."""
+         pick_less=False, threads=1, active=None, unclamped=False, rescan=False,
+         return_scanned=False):
+    """One synchronous sweep; returns (c_next, dN), plus the CSR entries of the swept
+    rows when ``return_scanned``.  ``active`` (bool/uint8 per vertex, optional) limits
+    the sweep to those vertices; the others keep their label."""
     offsets, indices, weights = _graph(offsets, indices, weights)
     n = offsets.size - 1
     c_prev = np.ascontiguousarray(c_prev, dtype=np.int32)
     c_next = np.empty(max(n, 1), dtype=np.int32)
-    dn = _load().oracle_move(n, offsets, indices, _wptr(weights),
-                             c_prev if n else np.zeros(1, np.int32), c_next, mode, k, e0,
-                             lmax, int(bool(pick_less)), threads)
+    act = None
+    if active is not None:
+        act = np.ascontiguousarray(np.asarray(active).astype(np.uint8))
+    scanned = ctypes.c_int64()
+    dn = _load().oracle_move_ex(n, offsets, indices, _wptr(weights),
+                                c_prev if n else np.zeros(1, np.int32), c_next,
+                                act.ctypes.data if act is not None and n else None, mode, k,
+                                e0, lmax, int(bool(pick_less)),
+                                _flags(unclamped=unclamped, rescan=rescan), threads,
+                                ctypes.byref(scanned))
+    if return_scanned:
+        return c_next[:n], int(dn), int(scanned.value)
     return c_next[:n], int(dn)
 
 
 def lpa(offsets, indices, weights=None, mode=MG, k=8, tol=0.05, max_iter=20, rho=8,
-        e0=64, lmax=256, labels_in=None, threads=1):
-    """Full run.  Returns dict(labels, changed, iterations, converged)."""
+        e0=64, lmax=256, labels_in=None, threads=1, prune=False, unclamped=False,
+        rescan=False):
+    """Full run.  Returns dict(labels, changed, scanned, iterations, converged); scanned
+    lists the CSR entries swept per iteration (all m unless ``prune``)."""
     offsets, indices, weights = _graph(offsets, indices, weights)
     n = offsets.size - 1
     labels = np.empty(max(n, 1), dtype=np.int32)
     changed = np.zeros(max(max_iter, 1), dtype=np.int64)
+    scanned = np.zeros(max(max_iter, 1), dtype=np.int64)
     it = ctypes.c_int32()
     conv = ctypes.c_int32()
     lin = None
     if labels_in is not None:
         lin_arr = np.ascontiguousarray(labels_in, dtype=np.int32)
         lin = lin_arr.ctypes.data
-    rc = _load().oracle_lpa(n, offsets, indices, _wptr(weights), mode, k, tol, max_iter,
-                            rho, e0, lmax, lin, labels, changed, ctypes.byref(it),
-                            ctypes.byref(conv), threads)
+    rc = _load().oracle_lpa_ex(n, offsets, indices, _wptr(weights), mode, k, tol, max_iter,
+                               rho, e0, lmax, _flags(prune, unclamped, rescan), lin, labels,
+                               changed, scanned, ctypes.byref(it), ctypes.byref(conv),
+                               threads)
     if rc != 0:
         raise ValueError("oracle_lpa: bad arguments")
     return {
         "labels": labels[:n].copy(),
         "changed": changed[: it.value].copy(),
+        "scanned": scanned[: it.value].copy(),
         "iterations": int(it.value),
         "converged": bool(conv.value),
     }

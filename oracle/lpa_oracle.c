@@ -34,6 +34,19 @@
  *     Alg. 3 skip j == i; a non-positive weight carries no vote).
  *  R10 convergence: after iteration l (0-based), stop iff pick-less was off in l and
  *     (double)dN / (double)N < tau; pick-less is on iff rho > 0 and l mod rho == 0.
+ *  R19 pruning (the unprocessed flags of Alg. 1), synchronous: iteration 0 sweeps every
+ *     vertex; iteration l+1 sweeps exactly the vertices j that appear in the row of a
+ *     vertex whose label changed in iteration l (every stored entry, self-loops and zero
+ *     weights included).  A vertex not swept keeps its label.
+ *  R20 the paper-literal sketch (ORACLE_UNCLAMPED; Alg. 2 without sharing): a slot whose
+ *     key equals c takes += w whatever its value; otherwise the lowest slot with value
+ *     exactly 0 takes (c, w); otherwise every slot takes -= w and c is dropped.  Values
+ *     may go negative; merges feed every slot with a non-zero value; the choice is the
+ *     largest positive value (R6).
+ *  R21 double scan (ORACLE_RESCAN, Sec. 4.4): after the sketch, K_{i->c} of every
+ *     occupied candidate c is summed over the row's valid entries, each leaf in CSR
+ *     order and the leaves along the stride-doubling tree; the choice is the largest
+ *     sum, ties to the smallest label.
  */
 #include "lpa_oracle.h"
 
@@ -102,10 +115,36 @@ static void sketchAccumulate(mg_sketch* S, int32_t c, float w) {
   }
 }
 
-/* merge(A, B): B's occupied slots, ascending, accumulated into A (Sec. 4.3; R5). */
-static void sketchMerge(mg_sketch* A, const mg_sketch* B) {
-  for (int32_t s = 0; s < B->k; ++s)
-    if (B->S_v[s] > 0.0f) sketchAccumulate(A, B->S_k[s], B->S_v[s]);
+/* sketchAccumulate as printed in Alg. 2 for a private sketch (R20): the key compare
+ * ignores the value, and a full sketch loses w from every slot. */
+static void sketchAccumulateLiteral(mg_sketch* S, int32_t c, float w) {
+  int has = 0;
+  for (int32_t s = 0; s < S->k; ++s) {
+    if (S->S_k[s] == c) {
+      S->S_v[s] = S->S_v[s] + w;
+      has = 1;
+    }
+  }
+  if (has) return;
+  int32_t sphi = lowest_empty_slot(S);
+  if (sphi >= 0) {
+    S->S_k[sphi] = c;
+    S->S_v[sphi] = w;
+    return;
+  }
+  for (int32_t s = 0; s < S->k; ++s) S->S_v[s] = S->S_v[s] - w;
+}
+
+/* merge(A, B): B's occupied slots, ascending, accumulated into A (Sec. 4.3; R5).  The
+ * literal variant feeds every slot of non-zero value (the merge loop of Alg. 1). */
+static void sketchMerge(mg_sketch* A, const mg_sketch* B, int literal) {
+  for (int32_t s = 0; s < B->k; ++s) {
+    if (literal) {
+      if (B->S_v[s] != 0.0f) sketchAccumulateLiteral(A, B->S_k[s], B->S_v[s]);
+    } else if (B->S_v[s] > 0.0f) {
+      sketchAccumulate(A, B->S_k[s], B->S_v[s]);
+    }
+  }
 }
 
 /* sketchMaxKey (Alg. 1, single scan Sec. 4.4; R6): -1 if the sketch is empty. */
@@ -144,7 +183,7 @@ static int valid_params(int32_t k, int32_t e0, int32_t lmax) {
 /* The MG sketch of a row given as a sequence of (label, weight); label < 0 marks a
  * position to skip (a self-loop at the caller), weight <= 0 is skipped as well (R9). */
 static void mg_row(const int32_t* lab, const float* w, int64_t d, int32_t k, int32_t e0,
-                   int32_t lmax, mg_sketch* out) {
+                   int32_t lmax, int literal, mg_sketch* out) {
   int32_t L = oracle_leaf_count(d, e0, lmax);
   mg_sketch* S = (mg_sketch*)malloc(sizeof(mg_sketch) * (size_t)L);
   /* each leaf folds its positions in ascending CSR order into an empty sketch */
@@ -153,23 +192,73 @@ static void mg_row(const int32_t* lab, const float* w, int64_t d, int32_t k, int
     for (int64_t p = leaf_begin(d, L, l); p < leaf_begin(d, L, l + 1); ++p) {
       float wp = w ? w[p] : 1.0f;
       if (lab[p] < 0 || !(wp > 0.0f)) continue;
-      sketchAccumulate(&S[l], lab[p], wp);
+      if (literal)
+        sketchAccumulateLiteral(&S[l], lab[p], wp);
+      else
+        sketchAccumulate(&S[l], lab[p], wp);
     }
   }
   /* stride-doubling tree: S[l] <- merge(S[l], S[l+s]) for l = 0 mod 2s */
   for (int32_t s = 1; s < L; s *= 2)
-    for (int32_t l = 0; l + s < L; l += 2 * s) sketchMerge(&S[l], &S[l + s]);
+    for (int32_t l = 0; l + s < L; l += 2 * s) sketchMerge(&S[l], &S[l + s], literal);
   *out = S[0];
   free(S);
+}
+
+/* Double scan (R21): the choice among the sketch's occupied candidates by their exact
+ * linking weight K_{i->c}; per leaf a sequential sum in CSR order, then the leaves'
+ * sums along the stride-doubling tree.  -1 when the sketch has no candidate. */
+static int32_t rescan_choice(const mg_sketch* S, const int32_t* lab, const float* w,
+                             int64_t d, int32_t e0, int32_t lmax) {
+  int32_t L = oracle_leaf_count(d, e0, lmax);
+  float* part = (float*)calloc((size_t)L * ORACLE_MAX_K, sizeof(float));
+  for (int32_t l = 0; l < L; ++l)
+    for (int64_t p = leaf_begin(d, L, l); p < leaf_begin(d, L, l + 1); ++p) {
+      float wp = w ? w[p] : 1.0f;
+      if (lab[p] < 0 || !(wp > 0.0f)) continue;
+      for (int32_t s = 0; s < S->k; ++s)
+        if (S->S_v[s] > 0.0f && S->S_k[s] == lab[p])
+          part[(size_t)l * ORACLE_MAX_K + s] = part[(size_t)l * ORACLE_MAX_K + s] + wp;
+    }
+  for (int32_t st = 1; st < L; st *= 2)
+    for (int32_t l = 0; l + st < L; l += 2 * st)
+      for (int32_t s = 0; s < S->k; ++s)
+        part[(size_t)l * ORACLE_MAX_K + s] =
+            part[(size_t)l * ORACLE_MAX_K + s] + part[(size_t)(l + st) * ORACLE_MAX_K + s];
+  int32_t best = -1;
+  float bestK = 0.0f;
+  for (int32_t s = 0; s < S->k; ++s) {
+    if (!(S->S_v[s] > 0.0f)) continue;
+    float K = part[s];
+    if (best < 0 || K > bestK || (K == bestK && S->S_k[s] < best)) {
+      best = S->S_k[s];
+      bestK = K;
+    }
+  }
+  free(part);
+  return best;
 }
 
 int oracle_mg_sketch(const int32_t* labels, const float* weights, int64_t d, int32_t k,
                      int32_t e0, int32_t lmax, int32_t* keys_out, float* vals_out) {
   if (!valid_params(k, e0, lmax) || d < 0 || (d > 0 && !labels)) return -1;
   mg_sketch S;
-  mg_row(labels, weights, d, k, e0, lmax, &S);
+  mg_row(labels, weights, d, k, e0, lmax, 0, &S);
   for (int32_t s = 0; s < k; ++s) {
     keys_out[s] = S.S_v[s] > 0.0f ? S.S_k[s] : -1;
+    vals_out[s] = S.S_v[s];
+  }
+  return 0;
+}
+
+int oracle_mg_sketch_ex(const int32_t* labels, const float* weights, int64_t d, int32_t k,
+                        int32_t e0, int32_t lmax, int32_t flags, int32_t* keys_out,
+                        float* vals_out) {
+  if (!valid_params(k, e0, lmax) || d < 0 || (d > 0 && !labels)) return -1;
+  mg_sketch S;
+  mg_row(labels, weights, d, k, e0, lmax, (flags & ORACLE_UNCLAMPED) != 0, &S);
+  for (int32_t s = 0; s < k; ++s) {
+    keys_out[s] = S.S_k[s];  /* raw slots: the literal sketch keeps stale keys */
     vals_out[s] = S.S_v[s];
   }
   return 0;
@@ -266,15 +355,16 @@ static int32_t* row_labels(int32_t i, const int64_t* off, const int32_t* idx,
 
 static int32_t choose_sketch(int32_t i, const int64_t* off, const int32_t* idx,
                              const float* w, const int32_t* C, int32_t mode, int32_t k,
-                             int32_t e0, int32_t lmax) {
+                             int32_t e0, int32_t lmax, int32_t flags) {
   int64_t d = off[i + 1] - off[i];
   int32_t* lab = row_labels(i, off, idx, C);
   const float* wrow = w ? w + off[i] : NULL;
   int32_t choice;
   if (mode == ORACLE_MG) {
     mg_sketch S;
-    mg_row(lab, wrow, d, k, e0, lmax, &S);
-    choice = sketchMaxKey(&S);
+    mg_row(lab, wrow, d, k, e0, lmax, (flags & ORACLE_UNCLAMPED) != 0, &S);
+    choice = (flags & ORACLE_RESCAN) ? rescan_choice(&S, lab, wrow, d, e0, lmax)
+                                     : sketchMaxKey(&S);
   } else {
     bm_state st = bm_row(lab, wrow, d, C[i], e0, lmax);
     choice = st.w > 0.0f ? st.c : -1;
@@ -300,18 +390,19 @@ int32_t oracle_choose(int32_t i, const int64_t* offsets, const int32_t* indices,
     free(touched);
     return c;
   }
-  return choose_sketch(i, offsets, indices, weights, c_prev, mode, k, e0, lmax);
+  return choose_sketch(i, offsets, indices, weights, c_prev, mode, k, e0, lmax, 0);
 }
 
 /* ------------------------------------------------------------------- the sweep */
 
-int64_t oracle_move(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
-                    const int32_t* c_prev, int32_t* c_next, int32_t mode, int32_t k,
-                    int32_t e0, int32_t lmax, int32_t pick_less, int32_t threads) {
-  int64_t dN = 0;
+int64_t oracle_move_ex(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
+                       const int32_t* c_prev, int32_t* c_next, const uint8_t* active,
+                       int32_t mode, int32_t k, int32_t e0, int32_t lmax, int32_t pick_less,
+                       int32_t flags, int32_t threads, int64_t* scanned_out) {
+  int64_t dN = 0, scanned = 0;
 #ifdef _OPENMP
   if (threads < 1) threads = 1;
-#pragma omp parallel num_threads(threads) reduction(+ : dN)
+#pragma omp parallel num_threads(threads) reduction(+ : dN, scanned)
 #endif
   {
     float* dense = NULL;
@@ -324,9 +415,14 @@ int64_t oracle_move(int32_t n, const int64_t* off, const int32_t* idx, const flo
 #pragma omp for schedule(dynamic, 1024)
 #endif
     for (int32_t i = 0; i < n; ++i) {
+      if (active && !active[i]) { /* not swept this iteration (R19) */
+        c_next[i] = c_prev[i];
+        continue;
+      }
+      scanned += off[i + 1] - off[i];
       int32_t c = (mode == ORACLE_EXACT)
                       ? exact_choice(i, off, idx, w, c_prev, dense, touched)
-                      : choose_sketch(i, off, idx, w, c_prev, mode, k, e0, lmax);
+                      : choose_sketch(i, off, idx, w, c_prev, mode, k, e0, lmax, flags);
       /* commit (Alg. 1 move step): change only to a different label, and under
        * pick-less only to a smaller one (Sec. 4.5) */
       if (c >= 0 && c != c_prev[i] && (!pick_less || c < c_prev[i])) {
@@ -339,20 +435,29 @@ int64_t oracle_move(int32_t n, const int64_t* off, const int32_t* idx, const flo
     free(dense);
     free(touched);
   }
+  if (scanned_out) *scanned_out = scanned;
   return dN;
+}
+
+int64_t oracle_move(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
+                    const int32_t* c_prev, int32_t* c_next, int32_t mode, int32_t k,
+                    int32_t e0, int32_t lmax, int32_t pick_less, int32_t threads) {
+  return oracle_move_ex(n, off, idx, w, c_prev, c_next, NULL, mode, k, e0, lmax, pick_less, 0,
+                        threads, NULL);
 }
 
 /* ------------------------------------------------------------------ the driver */
 
-int oracle_lpa(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
-               int32_t mode, int32_t k, double tol, int32_t max_iter, int32_t rho,
-               int32_t e0, int32_t lmax, const int32_t* labels_in, int32_t* labels_out,
-               int64_t* changed_out, int32_t* iterations_out, int32_t* converged_out,
-               int32_t threads) {
+int oracle_lpa_ex(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
+                  int32_t mode, int32_t k, double tol, int32_t max_iter, int32_t rho,
+                  int32_t e0, int32_t lmax, int32_t flags, const int32_t* labels_in,
+                  int32_t* labels_out, int64_t* changed_out, int64_t* scanned_out,
+                  int32_t* iterations_out, int32_t* converged_out, int32_t threads) {
   if (n < 0 || max_iter < 0 || rho < 0) return -1;
   if (mode != ORACLE_EXACT && mode != ORACLE_MG && mode != ORACLE_BM) return -1;
   if (mode == ORACLE_MG && !valid_params(k, e0, lmax)) return -1;
   if (mode == ORACLE_BM && !valid_params(1, e0, lmax)) return -1;
+  if ((flags & (ORACLE_UNCLAMPED | ORACLE_RESCAN)) && mode != ORACLE_MG) return -1;
   *iterations_out = 0;
   *converged_out = 0;
   if (n == 0) {
@@ -361,21 +466,46 @@ int oracle_lpa(int32_t n, const int64_t* off, const int32_t* idx, const float* w
   }
   int32_t* C = labels_out;
   int32_t* C2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  uint8_t* active = NULL;
+  if (flags & ORACLE_PRUNE) {
+    active = (uint8_t*)malloc((size_t)n);
+    memset(active, 1, (size_t)n); /* iteration 0 sweeps every vertex */
+  }
   /* C <- [0 .. |V|), or the caller's warm start */
   for (int32_t i = 0; i < n; ++i) C[i] = labels_in ? labels_in[i] : i;
   for (int32_t l = 0; l < max_iter; ++l) {
     int32_t pick_less = (rho > 0 && l % rho == 0);
-    int64_t dN = oracle_move(n, off, idx, w, C, C2, mode, k, e0, lmax, pick_less, threads);
+    int64_t scanned = 0;
+    int64_t dN = oracle_move_ex(n, off, idx, w, C, C2, active, mode, k, e0, lmax, pick_less,
+                                flags, threads, &scanned);
+    if (active) {
+      /* Alg. 1: a vertex that changed marks every vertex of its row unprocessed (R19) */
+      memset(active, 0, (size_t)n);
+      for (int32_t i = 0; i < n; ++i)
+        if (C2[i] != C[i])
+          for (int64_t p = off[i]; p < off[i + 1]; ++p) active[idx[p]] = 1;
+    }
     memcpy(C, C2, sizeof(int32_t) * (size_t)n);
     changed_out[l] = dN;
+    if (scanned_out) scanned_out[l] = scanned;
     *iterations_out = l + 1;
     if (!pick_less && (double)dN / (double)n < tol) {
       *converged_out = 1;
       break;
     }
   }
+  free(active);
   free(C2);
   return 0;
+}
+
+int oracle_lpa(int32_t n, const int64_t* off, const int32_t* idx, const float* w,
+               int32_t mode, int32_t k, double tol, int32_t max_iter, int32_t rho,
+               int32_t e0, int32_t lmax, const int32_t* labels_in, int32_t* labels_out,
+               int64_t* changed_out, int32_t* iterations_out, int32_t* converged_out,
+               int32_t threads) {
+  return oracle_lpa_ex(n, off, idx, w, mode, k, tol, max_iter, rho, e0, lmax, 0, labels_in,
+                       labels_out, changed_out, NULL, iterations_out, converged_out, threads);
 }
 
 /* ------------------------------------------------------------------ modularity */

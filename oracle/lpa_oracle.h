@@ -30,6 +30,10 @@ extern "C" {
 
 enum { ORACLE_EXACT = 0, ORACLE_MG = 1, ORACLE_BM = 2 };
 
+/* Variant flags: pruning by unprocessed flags (R19), the paper-literal sketch (R20) and
+ * the double scan (R21); the last two apply to MG only. */
+enum { ORACLE_PRUNE = 1, ORACLE_UNCLAMPED = 2, ORACLE_RESCAN = 4 };
+
 /* Number of leaves (partial sketches) for a row of d CSR positions. */
 int32_t oracle_leaf_count(int64_t d, int32_t e0, int32_t lmax);
 
@@ -40,6 +44,12 @@ int32_t oracle_leaf_count(int64_t d, int32_t e0, int32_t lmax);
 int oracle_mg_sketch(const int32_t* labels, const float* weights, int64_t d,
                      int32_t k, int32_t e0, int32_t lmax,
                      int32_t* keys_out, float* vals_out);
+
+/* As oracle_mg_sketch with variant flags (ORACLE_UNCLAMPED); the raw slots are returned
+ * (keys of empty slots as they stand). */
+int oracle_mg_sketch_ex(const int32_t* labels, const float* weights, int64_t d,
+                        int32_t k, int32_t e0, int32_t lmax, int32_t flags,
+                        int32_t* keys_out, float* vals_out);
 
 /* Weighted BM over one sequence, same leaf partition; (c#, w#) of the winning leaf. */
 int oracle_bm_sketch(const int32_t* labels, const float* weights, int64_t d,
@@ -57,6 +67,23 @@ int64_t oracle_move(int32_t n, const int64_t* offsets, const int32_t* indices,
                     const float* weights, const int32_t* c_prev, int32_t* c_next,
                     int32_t mode, int32_t k, int32_t e0, int32_t lmax,
                     int32_t pick_less, int32_t threads);
+
+/* One sweep over the vertices with active[i] != 0 (all when active is NULL); the others
+ * keep their label.  scanned_out (may be NULL) receives the CSR entries of swept rows. */
+int64_t oracle_move_ex(int32_t n, const int64_t* offsets, const int32_t* indices,
+                       const float* weights, const int32_t* c_prev, int32_t* c_next,
+                       const uint8_t* active, int32_t mode, int32_t k, int32_t e0,
+                       int32_t lmax, int32_t pick_less, int32_t flags, int32_t threads,
+                       int64_t* scanned_out);
+
+/* Full driver with variant flags; scanned_out (may be NULL) has room for max_iter
+ * entries and receives the CSR entries swept per iteration. */
+int oracle_lpa_ex(int32_t n, const int64_t* offsets, const int32_t* indices,
+                  const float* weights, int32_t mode, int32_t k, double tol,
+                  int32_t max_iter, int32_t rho, int32_t e0, int32_t lmax, int32_t flags,
+                  const int32_t* labels_in, int32_t* labels_out, int64_t* changed_out,
+                  int64_t* scanned_out, int32_t* iterations_out, int32_t* converged_out,
+                  int32_t threads);
 
 /* Full driver.  changed_out has room for max_iter entries.  labels_in may be NULL
  * (identity init).  Returns 0, or -1 for bad arguments. */
