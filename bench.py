@@ -42,7 +42,8 @@ UNIT = "edges/s"
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
 # hash of the sweep kernel source it was taken with.  If the source changes, traffic is
 # reported as null until a new capture is taken.
-SWEEP_TRAFFIC = {"src_sha256": None, "workload": None, "bytes_per_launch": None}
+SWEEP_TRAFFIC = {"src_sha256": "e8f9e7982f1732de8f721328d54116f0cacf86c9ea03ab10fa44a7ec6490d91f", "workload": "lfr26",
+                 "bytes_per_launch": 35120390741}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
@@ -408,7 +409,10 @@ def run_ours(args):
                      "kernel": "one sweep: sweep_hub_kernel and sweep_lane_kernel "
                                "<MGSketch<8>, weighted, runs> (concurrent, fork/join)",
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs"},
+                     "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs",
+                     # the second fraction: measured DRAM bytes of one sweep over its time
+                     "dram_achieved": (traffic / (launch_ms * 1e-3) / 1e9) if traffic else None,
+                     "dram_frac": (traffic / (launch_ms * 1e-3) / 1e9 / peak) if traffic else None},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_edges_all / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -56,6 +56,22 @@ typedef enum {
 #define LPA_VALIDATE 0x1u /* check the CSR (and labels_in) on the device first */
 #define LPA_TIMING 0x2u   /* time the sweep and binning kernels with CUDA events */
 #define LPA_MODULARITY 0x4u /* also compute the modularity of the result (Eq. 1) */
+/* Pruning by the unprocessed flags of Alg. 1, read synchronously: iteration 0 sweeps
+ * every vertex; iteration l+1 sweeps only the vertices listed in the row of a vertex
+ * whose label changed in iteration l, the others keep their label.  Fewer CSR
+ * positions are read (lpa_stats.scanned_iter); with pick-less off the MG and exact
+ * results equal the unpruned ones on symmetric graphs.  Runs only (lpa_detect*,
+ * lpa_plan_run); lpa_plan_sweep ignores it. */
+#define LPA_PRUNE 0x8u
+/* MG ablations of the paper (LPA_MG only, else LPA_EINVAL).  LPA_MG_UNCLAMPED: the
+ * accumulate exactly as printed in Alg. 2 for a private sketch -- a key match ignores
+ * the slot's value, a full sketch subtracts w from every slot and drops the label, so
+ * values may go negative; merges feed every slot of non-zero value; the choice is the
+ * largest positive value.  LPA_RESCAN: the double scan of Sec. 4.4 -- after the
+ * sketch, each candidate's exact K_{i->c} is summed (each leaf in CSR order, leaves
+ * along the merge tree) and the heaviest, ties to the smallest label, is chosen. */
+#define LPA_MG_UNCLAMPED 0x10u
+#define LPA_RESCAN 0x20u
 
 /* Largest max_iter accepted; lpa_stats.changed has this many entries. */
 #define LPA_MAX_ITER 1024
@@ -75,6 +91,8 @@ typedef struct {
   int32_t hubs;                     /* vertices swept by a whole CTA */
   double modularity;                /* Q of the result (LPA_MODULARITY), else 0 */
   float sweep_ms_iter[LPA_MAX_ITER]; /* device time of each sweep (LPA_TIMING) */
+  int64_t scanned_iter[LPA_MAX_ITER]; /* CSR positions swept by each sweep (m unless
+                                         LPA_PRUNE) */
 } lpa_stats;
 
 /* Options.  Call lpa_options_init first; it sets the paper's defaults (Sec. 5.1.2). */
@@ -86,8 +104,8 @@ typedef struct {
                                Default 64. */
   int32_t leaf_max;         /* Lmax: most partial sketches per row, power of two
                                <= 256.  Default 256. */
-  uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY.
-                               Default LPA_VALIDATE. */
+  uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY | LPA_PRUNE |
+                               LPA_MG_UNCLAMPED | LPA_RESCAN.  Default LPA_VALIDATE. */
   const int32_t* labels_in; /* device, n labels in [0, n) to start from; NULL = C[i]=i */
   void* stream;             /* cudaStream_t; NULL = legacy default stream */
   void* workspace;          /* device scratch of workspace_bytes bytes, 256-byte

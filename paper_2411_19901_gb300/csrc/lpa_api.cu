@@ -64,6 +64,7 @@ int64_t lane_cap(int64_t n, int64_t m, int e0) {
 // Workspace layout of a plan; offsets in bytes from the workspace base.
 struct Layout {
   size_t state, dn, dn_total, tmp;
+  size_t act, scanned, scan_total;  // pruning: two flag arrays, per-iteration counters
   // sketch modes
   size_t desc, wtab, hcnt, lcnt, hub_prefix, lane_prefix, hub_desc, lane_desc, counts;
   int64_t hub_cap, lane_cap;
@@ -85,6 +86,9 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int64_t tab_slots) {
   L.state = take(sizeof(DevState));
   L.dn = take(sizeof(unsigned long long) * LPA_MAX_ITER * kDnSlots);
   L.dn_total = take(sizeof(unsigned long long) * LPA_MAX_ITER);
+  L.act = take(2 * (size_t)n);
+  L.scanned = take(sizeof(unsigned long long) * LPA_MAX_ITER * kDnSlots);
+  L.scan_total = take(sizeof(unsigned long long) * LPA_MAX_ITER);
   L.tmp = take(sizeof(int32_t) * (size_t)n);
   if (mode == kExact) {
     L.cv0 = take(sizeof(int32_t) * (size_t)(n + 1));
@@ -161,6 +165,7 @@ struct lpa_plan_s {
   std::vector<cudaEvent_t> events;  // timing pairs, created on demand
   DevState* host_state = nullptr;   // page-locked mirrors
   unsigned long long* host_dn = nullptr;
+  unsigned long long* host_scan = nullptr;
   double* host_q = nullptr;
   unsigned long long* host_cls = nullptr;
 };
@@ -210,17 +215,22 @@ SweepArgs sweep_args(const lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next
   return a;
 }
 
+cudaError_t launch_sketch_sweep(const lpa_plan_s* p, const SweepArgs& a, cudaStream_t s_hub) {
+  const bool literal = (p->flags & LPA_MG_UNCLAMPED) != 0, rescan = (p->flags & LPA_RESCAN) != 0;
+  if (p->mode == kMG && (literal || rescan))
+    return launch_sweep_mg_variant(p->k, literal, rescan, p->w != nullptr, a, p->wp, p->stream,
+                                   s_hub);
+  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
+                           s_hub);
+}
+
 cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
   if (p->mode == kExact) return launch_sweep_exact(p->w != nullptr, a, p->stream);
-  if (!p->side)
-    return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
-                             p->stream);
+  if (!p->side) return launch_sketch_sweep(p, a, p->stream);
   // fork: the hub kernel on the side stream, the lane kernel on the plan's stream; join
   cudaError_t e = cudaEventRecord(p->fork_ev, p->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork_ev, 0);
-  if (e == cudaSuccess)
-    e = launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
-                          p->side);
+  if (e == cudaSuccess) e = launch_sketch_sweep(p, a, p->side);
   if (e == cudaSuccess) e = cudaEventRecord(p->join_ev, p->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->join_ev, 0);
   return e;
@@ -237,6 +247,7 @@ void destroy_plan(lpa_plan_s* p) {
   if (p->own_ws || p->own_tab) cudaStreamSynchronize(p->stream);
   if (p->host_state) cudaFreeHost(p->host_state);
   if (p->host_dn) cudaFreeHost(p->host_dn);
+  if (p->host_scan) cudaFreeHost(p->host_scan);
   if (p->host_q) cudaFreeHost(p->host_q);
   if (p->host_cls) cudaFreeHost(p->host_cls);
   delete p;
@@ -365,6 +376,8 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   const lpa_options& o = opt ? *opt : defaults;
   if (o.pl_period < 0) return fail(LPA_EINVAL, "pl_period = %d is negative", o.pl_period);
   if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
+  if ((o.flags & (LPA_MG_UNCLAMPED | LPA_RESCAN)) && mode != LPA_MG)
+    return fail(LPA_EINVAL, "LPA_MG_UNCLAMPED and LPA_RESCAN apply to LPA_MG only");
   if (o.leaf_max < 1 || o.leaf_max > kMaxLeaves || (o.leaf_max & (o.leaf_max - 1)))
     return fail(LPA_EINVAL, "leaf_max = %d must be a power of two in [1, %d]", o.leaf_max, kMaxLeaves);
   if (((uintptr_t)indices & 15) != 0 || ((uintptr_t)weights & 15) != 0)
@@ -391,6 +404,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   };
   cudaError_t ce = cudaMallocHost((void**)&p->host_state, sizeof(DevState));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_dn, sizeof(unsigned long long) * LPA_MAX_ITER);
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_scan, sizeof(unsigned long long) * LPA_MAX_ITER);
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_q, sizeof(double) * 4);
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_cls, sizeof(unsigned long long) * 32);
   if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
@@ -503,15 +517,32 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
   LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));  // done, iterations, converged, err
   LPA_CUDA(launch_fill_u64(p->dn, 0ull, (int64_t)max_iter * kDnSlots, s));
   LPA_CUDA(launch_init_labels(labels_out, p->labels_in, n, s));
+  // pruning: act[0] = every vertex unprocessed before iteration 0; iteration l reads
+  // act[l & 1] and marks act[(l + 1) & 1]
+  const bool prune = (p->flags & LPA_PRUNE) != 0;
+  uint8_t* act = (uint8_t*)(p->ws + p->lay.act);
+  unsigned long long* scanned = prune ? (unsigned long long*)(p->ws + p->lay.scanned) : nullptr;
+  unsigned long long* scan_total = (unsigned long long*)(p->ws + p->lay.scan_total);
+  if (prune) {
+    LPA_CUDA(launch_fill_u8(act, 1, n, s));
+    LPA_CUDA(launch_fill_u64(scanned, 0ull, (int64_t)max_iter * kDnSlots, s));
+  }
   int32_t* buf[2] = {labels_out, p->tmp};
   for (int l = 0; l < max_iter; ++l) {
     const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
-    const SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
-                                   p->dn + (int64_t)l * kDnSlots, &p->st->done);
+    SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
+                             p->dn + (int64_t)l * kDnSlots, &p->st->done);
+    if (prune) {
+      a.act_in = act + (int64_t)(l & 1) * n;
+      a.act_out = act + (int64_t)((l + 1) & 1) * n;
+      a.scanned = scanned + (int64_t)l * kDnSlots;
+    }
     if (timing) LPA_CUDA(cudaEventRecord(p->events[2 + 2 * l], s));
+    if (prune) LPA_CUDA(launch_fill_u8(a.act_out, 0, n, s));
     LPA_CUDA(launch_one_sweep(p, a));
     if (timing) LPA_CUDA(cudaEventRecord(p->events[3 + 2 * l], s));
-    LPA_CUDA(launch_converge(p->st, p->dn, p->dn_total, l, pick_less, tol, n, s));
+    LPA_CUDA(launch_converge(p->st, p->dn, p->dn_total, scanned, scan_total, l, pick_less, tol,
+                             n, s));
   }
   LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
   const bool want_q = (p->flags & LPA_MODULARITY) != 0;
@@ -524,6 +555,9 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
   if (max_iter > 0)
     LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn_total, sizeof(unsigned long long) * max_iter,
                              cudaMemcpyDeviceToHost, s));
+  if (max_iter > 0 && prune)
+    LPA_CUDA(cudaMemcpyAsync(p->host_scan, scan_total, sizeof(unsigned long long) * max_iter,
+                             cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
   const int iters = p->host_state->iterations;
   if (iters < 0 || iters > max_iter) return fail(LPA_EINTERNAL, "device reported %d iterations", iters);
@@ -532,7 +566,11 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
     stats->iterations = iters;
     stats->converged = p->host_state->converged;
     for (int l = 0; l < iters; ++l) stats->changed[l] = (int64_t)p->host_dn[l];
-    stats->edges_scanned = (int64_t)iters * p->m;
+    stats->edges_scanned = 0;
+    for (int l = 0; l < iters; ++l) {
+      stats->scanned_iter[l] = prune ? (int64_t)p->host_scan[l] : p->m;
+      stats->edges_scanned += stats->scanned_iter[l];
+    }
     stats->sweep_launches = iters;
     stats->device_bytes = p->ws_bytes + (p->own_tab ? (size_t)(2 * p->hub_edges) * 8 : 0);
     stats->chunks = (int32_t)p->nchunks;

@@ -33,9 +33,14 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
   __shared__ float s_bv[kThreads / 32];
   __shared__ int s_bk[kThreads / 32];
   const int tid = threadIdx.x;
+  __shared__ int s_changed;
   const int v = a.hubs[h];
   const int64_t base = a.off[v];
   const int64_t d = a.off[v + 1] - base;
+  if (a.act_in != nullptr && !a.act_in[v]) {  // not marked unprocessed: keep the label
+    if (tid == 0) a.c_next[v] = a.c_prev[v];
+    return;
+  }
   int lg = 1;
   while (((int64_t)1 << (lg + 1)) <= 2 * d) ++lg;
   const int64_t cap = (int64_t)1 << lg;  // largest power of two <= 2d (> d)
@@ -95,7 +100,14 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
     const int own = a.c_prev[v];
     const int nl = commit(bv > 0.f ? bk : -1, own, a.pick_less);
     a.c_next[v] = nl;
+    s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn, 1ull);
+    if (a.scanned) atomicAdd(a.scanned + (h & (kDnSlots - 1)), (unsigned long long)d);
+  }
+  if (a.act_out != nullptr) {  // a moved vertex marks its neighbours unprocessed
+    __syncthreads();
+    if (s_changed)
+      for (int64_t q = base + tid; q < base + d; q += kThreads) a.act_out[__ldg(a.idx + q)] = 1;
   }
 }
 
@@ -129,8 +141,9 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
   __syncthreads();
   int changed = 0;
   int nl = 0;
+  const bool act = tid < nv && (a.act_in == nullptr || a.act_in[v0 + tid] != 0);
   if (tid < nv) {
-    const int b = s_start[tid], d = s_start[tid + 1] - b;
+    const int b = s_start[tid], d = act ? s_start[tid + 1] - b : 0;
     int best = -1;
     if (d > 0) {
       int lg = 1;
@@ -164,6 +177,18 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
   }
   const int cnt = __syncthreads_count(changed);
   if (tid == 0 && cnt > 0) atomicAdd(a.dn, (unsigned long long)cnt);
+  if (a.act_out != nullptr) {
+    if (changed)
+      for (int q = s_start[tid]; q < s_start[tid + 1]; ++q) a.act_out[__ldg(a.idx + base + q)] = 1;
+    if (tid < 32) {
+      unsigned part = 0;
+      for (int t = tid; t < nv; t += 32)
+        if (a.act_in[v0 + t]) part += (unsigned)(s_start[t + 1] - s_start[t]);
+      part = __reduce_add_sync(kFull, part);
+      if (tid == 0 && part > 0)
+        atomicAdd(a.scanned + (chunk & (kDnSlots - 1)), (unsigned long long)part);
+    }
+  }
 }
 
 template <bool WT>

@@ -129,6 +129,131 @@ struct MGSketch {
   }
 };
 
+// ------------------------------------------------------ paper-literal MG sketch
+
+// sketchAccumulate as printed in Alg. 2 for a private sketch (the LPA_MG_UNCLAMPED
+// ablation): a slot whose key equals c takes += w whatever its value; otherwise the
+// lowest slot of value exactly 0 takes (c, w); otherwise every slot loses w and c is
+// dropped.  Values may go negative; merges feed every slot of non-zero value; the
+// choice is the largest positive value.  Consecutive equal labels are not foldable
+// (a full sketch drops the first and may then have room for the second).
+template <int K>
+struct MGLiteral {
+  int key[K];
+  float val[K];
+  static constexpr int kSlots = K;
+  static constexpr bool kRunMergeable = false;
+
+  __device__ __forceinline__ void init(int /*own*/) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      key[s] = -1;
+      val[s] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(int c, float w) {
+    bool hit = false;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const bool m = (key[s] == c);
+      if (m) val[s] = val[s] + w;
+      hit = hit || m;
+    }
+    if (hit) return;
+    unsigned em = 0;
+#pragma unroll
+    for (int s = 0; s < K; ++s) em |= (val[s] == 0.f ? 1u : 0u) << s;
+    if (em != 0u) {
+      const int s0 = __ffs(em) - 1;
+#pragma unroll
+      for (int s = 0; s < K; ++s) {
+        key[s] = (s == s0) ? c : key[s];
+        val[s] = (s == s0) ? w : val[s];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < K; ++s) val[s] = val[s] - w;
+    }
+  }
+  __device__ __forceinline__ void merge_from(const int* bk, const float* bv) {
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+      if (bv[s] != 0.f) add(bk[s], bv[s]);
+  }
+  __device__ __forceinline__ void shfl_merge(int s, bool take) {
+    int bk[K];
+    float bv[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      bk[q] = __shfl_down_sync(kFullMask, key[q], s);
+      bv[q] = __shfl_down_sync(kFullMask, val[q], s);
+    }
+    if (take) merge_from(bk, bv);
+  }
+  __device__ __forceinline__ int choose() const {
+    int best = -1;
+    float bv = 0.f;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const bool better = (val[s] > bv) || (val[s] == bv && val[s] > 0.f && key[s] < best);
+      best = better ? key[s] : best;
+      bv = better ? val[s] : bv;
+    }
+    return best;
+  }
+  __device__ __forceinline__ void store(int* k, float* v) const {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      k[s] = key[s];
+      v[s] = val[s];
+    }
+  }
+  __device__ __forceinline__ void load(const int* k, const float* v) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      key[s] = k[s];
+      val[s] = v[s];
+    }
+  }
+};
+
+// ------------------------------------------------------------- double scan
+
+// Second scan of Sec. 4.4 over one leaf: part[s] += w for every valid position whose
+// neighbour label equals candidate ck[s] (ck[s] = -1: no candidate), in CSR order.
+template <int K, bool WT>
+__device__ __forceinline__ void rescan_range(float (&part)[K], const int (&ck)[K],
+                                             const int32_t* __restrict__ idx,
+                                             const float* __restrict__ wts,
+                                             const int32_t* __restrict__ lab, int self,
+                                             int64_t b, int64_t e) {
+  for (int64_t p = b; p < e; ++p) {
+    const int j = __ldg(idx + p);
+    const float w = WT ? __ldg(wts + p) : 1.f;
+    if (j == self || !(w > 0.f)) continue;
+    const int c = __ldg(lab + j);
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+      if (ck[s] == c) part[s] = part[s] + w;
+  }
+}
+
+// The candidate of largest summed weight, ties to the smallest label; -1 if none.
+template <int K>
+__device__ __forceinline__ int rescan_pick(const float (&part)[K], const int (&ck)[K]) {
+  int best = -1;
+  float bk = 0.f;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    if (ck[s] < 0) continue;
+    if (best < 0 || part[s] > bk || (part[s] == bk && ck[s] < best)) {
+      best = ck[s];
+      bk = part[s];
+    }
+  }
+  return best;
+}
+
 // ---------------------------------------------------------------- BM state
 
 // Weighted Boyer-Moore candidate (Sec. 4.7, Alg. 3) as printed: same label adds, a

@@ -115,6 +115,13 @@ struct SweepArgs {
   float* tab_vals;
   unsigned long long* dn;  // dN counters of this sweep (kDnSlots for the warp kernels)
   const int32_t* done;     // skip the sweep if *done (null: never)
+  // Pruning (the unprocessed flags of Alg. 1), null when off: only vertices with
+  // act_in[v] != 0 are swept (the rest keep their label); a vertex whose label changes
+  // sets act_out[j] = 1 for every j in its row; scanned (kDnSlots counters) receives
+  // the CSR positions of the swept rows.
+  const uint8_t* act_in;
+  uint8_t* act_out;
+  unsigned long long* scanned;
   int32_t nchunks;
   int32_t nhubs;
   int32_t pick_less;
@@ -150,6 +157,11 @@ cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, cons
                               cudaStream_t s, cudaStream_t s_hub);
 cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
                               cudaStream_t s, cudaStream_t s_hub);
+// MG ablations (at least one of literal, rescan set): paper-literal accumulate and / or
+// double scan, hub kernel on s_hub and lane kernel on s as launch_sweep_warp.
+cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, bool weighted,
+                                    const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                                    cudaStream_t s_hub);
 // Weight profile: out[0] = 1 if every weight is integer-valued (AND), out[1] = largest
 // weight's bits, out[2] = largest row length.  out must be zeroed except out[0] = 1.
 cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
@@ -184,10 +196,13 @@ cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float*
 cudaError_t launch_bin(const BinArgs& b, DevState* st, cudaStream_t s, bool write_pass);
 cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n,
                                cudaStream_t s);
-// dn: kDnSlots counters per iteration; the test sums iteration l's slots into dn_total[l].
+// dn: kDnSlots counters per iteration; the test sums iteration l's slots into dn_total[l]
+// (and, when scanned is not null, iteration l's scanned slots into scan_total[l]).
 cudaError_t launch_converge(DevState* st, const unsigned long long* dn,
-                            unsigned long long* dn_total, int l, int pick_less, double tol,
+                            unsigned long long* dn_total, const unsigned long long* scanned,
+                            unsigned long long* scan_total, int l, int pick_less, double tol,
                             int32_t n, cudaStream_t s);
+cudaError_t launch_fill_u8(uint8_t* p, uint8_t value, int64_t count, cudaStream_t s);
 cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp,
                             int32_t n, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s);

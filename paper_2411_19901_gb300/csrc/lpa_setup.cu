@@ -390,12 +390,18 @@ __global__ void init_labels_kernel(int32_t* c, const int32_t* labels_in, int32_t
 // Convergence test after sweep l (Alg. 1): dN is the sum of the sweep's counters; stop
 // iff pick-less was off and dN/N < tau.
 __global__ void converge_kernel(DevState* st, const unsigned long long* dn,
-                                unsigned long long* dn_total, int l, int pick_less, double tol,
+                                unsigned long long* dn_total, const unsigned long long* scanned,
+                                unsigned long long* scan_total, int l, int pick_less, double tol,
                                 int32_t n) {
   if (threadIdx.x != 0 || st->done) return;
   unsigned long long tot = 0;
   for (int i = 0; i < kDnSlots; ++i) tot += dn[(int64_t)l * kDnSlots + i];
   dn_total[l] = tot;
+  if (scanned) {
+    unsigned long long sc = 0;
+    for (int i = 0; i < kDnSlots; ++i) sc += scanned[(int64_t)l * kDnSlots + i];
+    scan_total[l] = sc;
+  }
   st->iterations = l + 1;
   if (!pick_less && (double)tot / (double)n < tol) {
     st->done = 1;
@@ -421,6 +427,12 @@ __global__ void finalize_kernel(const DevState* st, int32_t* out, const int32_t*
 __global__ void fill_i32_kernel(int32_t* p, int32_t value, int64_t count) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = value;
+}
+
+__global__ void fill_u8_kernel(uint8_t* p, uint8_t value, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    p[i] = value;
 }
 
 __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long value, int64_t count) {
@@ -577,9 +589,10 @@ cudaError_t launch_init_labels(int32_t* c, const int32_t* labels_in, int32_t n, 
 }
 
 cudaError_t launch_converge(DevState* st, const unsigned long long* dn,
-                            unsigned long long* dn_total, int l, int pick_less, double tol,
+                            unsigned long long* dn_total, const unsigned long long* scanned,
+                            unsigned long long* scan_total, int l, int pick_less, double tol,
                             int32_t n, cudaStream_t s) {
-  converge_kernel<<<1, 32, 0, s>>>(st, dn, dn_total, l, pick_less, tol, n);
+  converge_kernel<<<1, 32, 0, s>>>(st, dn, dn_total, scanned, scan_total, l, pick_less, tol, n);
   count_launch();
   return cudaGetLastError();
 }
@@ -595,6 +608,13 @@ cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   fill_i32_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u8(uint8_t* p, uint8_t value, int64_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  fill_u8_kernel<<<grid_for(count, 256), 256, 0, s>>>(p, value, count);
   count_launch();
   return cudaGetLastError();
 }

@@ -50,9 +50,9 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
 // warps and through shared memory across warps.  RUNS folds runs of equal consecutive
 // labels as one add (MG only; the caller enables it when every sum of a row's weights is
 // exact in fp32, so the bits do not change).
-template <class S, bool WT, bool RUNS>
+template <class S, bool WT, bool RUNS, bool RESCAN = false>
 __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPlan p) {
-  constexpr bool kRuns = RUNS && S::kRunMergeable;
+  constexpr bool kRuns = RUNS && S::kRunMergeable && !RESCAN;
   if (a.done != nullptr && *a.done) return;
   __shared__ int sk[(kThreads / 32) * 32];
   __shared__ float sv[(kThreads / 32) * 32];
@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   const int64_t base = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
   const int64_t d = h.w;
   const int L = leaf_count(d, a.e0, a.lmax);
+  if (a.act_in != nullptr && !a.act_in[v]) {  // not marked unprocessed: keep the label
+    if (tid == 0) a.c_next[v] = a.c_prev[v];
+    return;
+  }
   const int own = a.c_prev[v];
   S st;
   st.init(own);
@@ -71,10 +75,61 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   const int Lw = L < 32 ? L : 32;
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
   if (L > 32) cross_warp_tree<S>(st, L, tid, sk, sv);
+  int choice = -1;
+  if constexpr (RESCAN) {
+    // double scan: thread 0's candidates to every thread, per-leaf sums, the same tree
+    constexpr int K = S::kSlots;
+    if (tid == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) sk[q] = st.val[q] > 0.f ? st.key[q] : -1;
+    __syncthreads();
+    int ck[K];
+    float part[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      ck[q] = sk[q];
+      part[q] = 0.f;
+    }
+    __syncthreads();
+    if (tid < L)
+      rescan_range<K, WT>(part, ck, a.idx, a.w, a.c_prev, v, base + (tid * d) / L,
+                          base + ((tid + 1) * d) / L);
+    for (int s = 1; s < Lw; s <<= 1)
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const float y = __shfl_down_sync(kFullMask, part[q], s);
+        if (tid < L && (lane & (2 * s - 1)) == 0) part[q] = part[q] + y;
+      }
+    if (L > 32) {
+      const int nw = L / 32;
+      if (lane == 0 && (tid >> 5) < nw)
+#pragma unroll
+        for (int q = 0; q < K; ++q) sv[(tid >> 5) * K + q] = part[q];
+      __syncthreads();
+      if (tid == 0) {
+        for (int s = 1; s < nw; s <<= 1)
+          for (int w = 0; w + s < nw; w += 2 * s)
+            for (int q = 0; q < K; ++q) sv[w * K + q] = sv[w * K + q] + sv[(w + s) * K + q];
+#pragma unroll
+        for (int q = 0; q < K; ++q) part[q] = sv[q];
+      }
+    }
+    if (tid == 0) choice = rescan_pick<K>(part, ck);
+  } else {
+    if (tid == 0) choice = st.choose();
+  }
+  __shared__ int s_changed;
   if (tid == 0) {
-    const int nl = commit_label(st.choose(), own, a.pick_less);
+    const int nl = commit_label(choice, own, a.pick_less);
     a.c_next[v] = nl;
+    s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn + (blockIdx.x & (kDnSlots - 1)), 1ull);
+    if (a.scanned) atomicAdd(a.scanned + (blockIdx.x & (kDnSlots - 1)), (unsigned long long)d);
+  }
+  if (a.act_out != nullptr) {  // a moved vertex marks its neighbours unprocessed
+    __syncthreads();
+    if (s_changed)
+      for (int64_t q = base + tid; q < base + d; q += kThreads) a.act_out[__ldg(a.idx + q)] = 1;
   }
 }
 
@@ -82,9 +137,9 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
 // mid vertex whose L lanes are aligned inside the warp).  Lanes of one warp may belong to
 // vertices of different L: every lane runs the warp's largest L, merging only below its
 // own.  Warps are independent, so a CTA of kLaneThreads holds as few of them as possible.
-template <class S, bool WT, bool RUNS>
+template <class S, bool WT, bool RUNS, bool RESCAN = false>
 __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
-  constexpr bool kRuns = RUNS && S::kRunMergeable;
+  constexpr bool kRuns = RUNS && S::kRunMergeable && !RESCAN;
   if (a.done != nullptr && *a.done) return;
   const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -98,44 +153,91 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
     leaf = (l.w >> kLaneLeafShift) & 31;
     L = 1 << (l.w >> kLaneLgShift);
   }
+  const bool act = v >= 0 && (a.act_in == nullptr || a.act_in[v] != 0);
   S st;
   int own = -1;
   if (v >= 0) {
     own = a.c_prev[v];
     st.init(own);
-    fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
+    if (act) fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
   } else {
     st.init(-1);
   }
   const int Lw = __reduce_max_sync(kFullMask, L);
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, v >= 0 && s < L && (leaf & (2 * s - 1)) == 0);
+  int choice = -1;
+  if constexpr (RESCAN) {
+    // double scan: the leader's candidates to the vertex's lanes, per-leaf sums of
+    // their exact weights, summed along the same stride-doubling tree
+    constexpr int K = S::kSlots;
+    int ck[K];
+    float part[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      ck[q] = __shfl_sync(kFullMask, st.val[q] > 0.f ? st.key[q] : -1, lane - leaf);
+      part[q] = 0.f;
+    }
+    if (act) rescan_range<K, WT>(part, ck, a.idx, a.w, a.c_prev, v, lo, lo + len);
+    for (int s = 1; s < Lw; s <<= 1)
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const float y = __shfl_down_sync(kFullMask, part[q], s);
+        if (v >= 0 && s < L && (leaf & (2 * s - 1)) == 0) part[q] = part[q] + y;
+      }
+    choice = rescan_pick<K>(part, ck);
+  } else {
+    choice = st.choose();
+  }
   int changed = 0;
   if (v >= 0 && leaf == 0) {
-    const int nl = commit_label(st.choose(), own, a.pick_less);
+    const int nl = commit_label(choice, own, a.pick_less);
     a.c_next[v] = nl;
     changed = nl != own;
   }
   const int wsum = __reduce_add_sync(kFullMask, changed);
   if (lane == 0 && wsum > 0)
     atomicAdd(a.dn + ((q >> 5) & (kDnSlots - 1)), (unsigned long long)wsum);
+  if (a.act_out != nullptr) {
+    // the vertex's leader knows whether it moved; each of its lanes marks its own leaf
+    const int moved = __shfl_sync(kFullMask, changed, lane - leaf);
+    if (v >= 0 && moved)
+      for (int64_t p2 = lo; p2 < lo + len; ++p2) a.act_out[__ldg(a.idx + p2)] = 1;
+    const unsigned sc = __reduce_add_sync(kFullMask, act ? (unsigned)len : 0u);
+    if (lane == 0 && sc > 0) atomicAdd(a.scanned + ((q >> 5) & (kDnSlots - 1)), (unsigned long long)sc);
+  }
 }
 
 // One sweep: the hub kernel on s_hub and the lane kernel on s (the caller orders the two
 // streams; they may be the same stream).  Both write disjoint entries of c_next and add to
 // the same dN counters.
-template <class S, bool WT, bool RUNS>
+template <class S, bool WT, bool RUNS, bool RESCAN = false>
 cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
                                cudaStream_t s_hub) {
   if (p.nhubs > 0) {
-    sweep_hub_kernel<S, WT, RUNS><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
+    sweep_hub_kernel<S, WT, RUNS, RESCAN><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
     count_launch();
   }
   const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
   if (lane_ctas > 0) {
-    sweep_lane_kernel<S, WT, RUNS><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    sweep_lane_kernel<S, WT, RUNS, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
     count_launch();
   }
   return cudaGetLastError();
+}
+
+// The MG ablation variants of one k: paper-literal accumulate and / or double scan.
+template <int K>
+cudaError_t launch_mg_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+                              const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
+  if (literal) {
+    if (rescan)
+      return weighted ? launch_warp_kernel<MGLiteral<K>, true, false, true>(a, p, s, s_hub)
+                      : launch_warp_kernel<MGLiteral<K>, false, false, true>(a, p, s, s_hub);
+    return weighted ? launch_warp_kernel<MGLiteral<K>, true, false, false>(a, p, s, s_hub)
+                    : launch_warp_kernel<MGLiteral<K>, false, false, false>(a, p, s, s_hub);
+  }
+  return weighted ? launch_warp_kernel<MGSketch<K>, true, false, true>(a, p, s, s_hub)
+                  : launch_warp_kernel<MGSketch<K>, false, false, true>(a, p, s, s_hub);
 }
 
 // The four instantiations of one sketch type: weighted or not, runs folded or not.

@@ -21,6 +21,9 @@ MODES = {"exact": LPA_EXACT, "mg": LPA_MG, "bm": LPA_BM}
 LPA_VALIDATE = 0x1
 LPA_TIMING = 0x2
 LPA_MODULARITY = 0x4
+LPA_PRUNE = 0x8
+LPA_MG_UNCLAMPED = 0x10
+LPA_RESCAN = 0x20
 LPA_MAX_ITER = 1024
 
 STATUS = {0: "LPA_OK", -1: "LPA_EINVAL", -2: "LPA_ENOMEM", -3: "LPA_ECUDA",
@@ -48,6 +51,7 @@ class lpa_stats(ctypes.Structure):
         ("hubs", ctypes.c_int32),
         ("modularity", ctypes.c_double),
         ("sweep_ms_iter", ctypes.c_float * LPA_MAX_ITER),
+        ("scanned_iter", ctypes.c_int64 * LPA_MAX_ITER),
     ]
 
     def to_dict(self) -> dict:
@@ -66,6 +70,7 @@ class lpa_stats(ctypes.Structure):
             "hubs": int(self.hubs),
             "modularity": float(self.modularity),
             "sweep_ms_iter": [float(x) for x in self.sweep_ms_iter[:it]],
+            "scanned": [int(x) for x in self.scanned_iter[:it]],
         }
 
 
@@ -182,13 +187,14 @@ def lpa_options_init() -> lpa_options:
 
 def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=False,
                  modularity=False, labels_in=None, stream=None, workspace=None,
-                 workspace_bytes=0) -> lpa_options:
+                 workspace_bytes=0, prune=False, unclamped=False, rescan=False) -> lpa_options:
     o = lpa_options_init()
     o.pl_period = pl_period
     o.leaf_e0 = leaf_e0
     o.leaf_max = leaf_max
     o.flags = ((LPA_VALIDATE if validate else 0) | (LPA_TIMING if timing else 0)
-               | (LPA_MODULARITY if modularity else 0))
+               | (LPA_MODULARITY if modularity else 0) | (LPA_PRUNE if prune else 0)
+               | (LPA_MG_UNCLAMPED if unclamped else 0) | (LPA_RESCAN if rescan else 0))
     o.labels_in = _ptr(labels_in)
     o.stream = _stream_handle(stream)
     if workspace is not None:
