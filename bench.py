@@ -54,7 +54,13 @@ WORKLOADS = {
               "duplicates merged with summed weights, seed 0",
     "pp1000": "planted partition, 1000 vertices in 10 communities, p_in=0.1, p_out=0.005, "
               "unit weights, seed 0",
+    "sbm256": "batched form: graphs 0..255 of the uneven planted-partition family (n "
+              "log-uniform in [100, 2e5], mean degree U[8, 64], communities log-uniform in "
+              "[4, 500] capped at n/20, 80 % internal, unit weights), seed 0",
+    "sbm4096": "batched form: graphs 0..4095 of the same family, seed 0",
 }
+BATCH_COUNT = {"sbm256": 256, "sbm4096": 4096}
+BATCH_METRIC = "MG8-LPA batched graphs/s"
 
 
 def make_graph(name: str) -> synth.Graph:
@@ -241,9 +247,49 @@ def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int):
 # ------------------------------------------------------------------ arms
 
 
+def oracle_batch_rate(gs, mode: str, seconds: float):
+    """Full oracle runs, graph after graph, on all host cores for about ``seconds``."""
+    import oracle
+
+    om = {"mg": oracle.MG, "bm": oracle.BM, "exact": oracle.EXACT}[mode]
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    for g in gs:
+        oracle.lpa(g.offsets, g.indices, g.weights, mode=om, k=8, tol=0.05, max_iter=20,
+                   threads=threads)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, threads
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload in BATCH_COUNT:
+        gs = make_batch(BATCH_COUNT[args.workload])
+        rates = []
+        for step in range(args.warmup + args.steps):
+            rate, done, dt, threads = oracle_batch_rate(gs, args.mode, 10.0)
+            if step >= args.warmup:
+                rates.append(rate)
+        value = sum(rates) / len(rates)
+        sample = f"full oracle runs of the batch's first graphs, about 10 s per step"
+        print(json.dumps({
+            "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * len(gs) / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "graphs": len(gs), "mode": args.mode, "k": 8},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }), flush=True)
         return
     g = make_graph(args.workload)
     import oracle  # noqa: F401  (the reference arm is the CPU oracle)
@@ -432,6 +478,153 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _gen_member(g):
+    return synth.sbm_member(g, seed=0)
+
+
+def make_batch(count: int):
+    """The batch's graphs, generated on all host cores (a spawn pool: no CUDA state is
+    inherited by the workers)."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(min(count, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_member, range(count), chunksize=4)
+
+
+def run_batch(args):
+    """Batched form: one lpa_batch_detect over the whole batch per step, against one
+    lpa_detect_ex per graph.  Unit: graphs per second over the batch."""
+    world, rank, local = dist_env()
+    t0 = time.perf_counter()
+    gs = make_batch(BATCH_COUNT[args.workload])
+    gen_s = time.perf_counter() - t0
+    import torch
+
+    import paper_2411_19901_gb300 as lpa
+    from paper_2411_19901_gb300 import build
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        barrier = dist.barrier
+    else:
+        def barrier():
+            pass
+    dev = torch.device("cuda", local)
+    build.build()
+    count = len(gs)
+    n_all = sum(g.n for g in gs)
+    m_all = sum(g.m for g in gs)
+    h = [(torch.from_numpy(g.offsets), torch.from_numpy(g.indices)) for g in gs]
+    d = [(o.to(dev), i.to(dev), None, torch.empty(g.n, dtype=torch.int32, device=dev))
+         for (o, i), g in zip(h, gs)]
+    stream = torch.cuda.current_stream(dev)
+    opt = lpa.make_options(validate=False, stream=stream)
+
+    def step():
+        return lpa.lpa_batch_detect(d, mode=args.mode, k=8, tol=0.05, max_iter=20, opt=opt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = ClockSampler(physical_gpu_index(local))
+    launches0 = lpa.lpa_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    time.sleep(0.5)
+    torch.cuda.synchronize(dev)
+    clocks.mark("start")
+    ev0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark("end")
+    barrier()
+    clk = clocks.stop()
+    launches = lpa.lpa_launch_count() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stats = results[-1][0]
+    # one call per graph (the same work, one plan and run per graph)
+    one_steps = 1
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(one_steps):
+        for (o, i, w, out) in d:
+            st = lpa.lpa_stats()
+            lpa.lpa_detect_ex(o, i, w, int(o.numel() - 1), int(i.numel()), args.mode, 8, 0.05,
+                              20, out, st, opt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    one_ms = e0.elapsed_time(e1) / one_steps
+    # end to end: host graphs in, labels out, every step
+    pin = world == 1
+    hp = [(o.pin_memory(), i.pin_memory()) if pin else (o, i) for (o, i) in h]
+    h_out = [torch.empty(g.n, dtype=torch.int32, pin_memory=pin) for g in gs]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host = time.perf_counter()
+    e2.record(stream)
+    for _ in range(e2e_steps):
+        for (o, i), (do, di, _, _) in zip(hp, d):
+            do.copy_(o, non_blocking=True)
+            di.copy_(i, non_blocking=True)
+        step()
+        for ho, (_, _, _, dout) in zip(h_out, d):
+            ho.copy_(dout, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = max(e2.elapsed_time(e3), 1e3 * (time.perf_counter() - t_host)) / e2e_steps
+    (elapsed_ms, e2e_ms), (graphs_all, e2e_graphs_all) = aggregate_over_ranks(
+        [elapsed_ms, e2e_ms * e2e_steps], [count * args.steps, count * e2e_steps], world, dev)
+    if rank != 0:
+        return
+    iters = [s["iterations"] for s in stats]
+    useful = sum(it * (8 * g.m + 16 * g.n) for it, g in zip(iters, gs))
+    cpu = None
+    if world == 1:
+        rate, done, dt, threads = oracle_batch_rate(gs, args.mode, 10.0)
+        cpu = {"value": rate, "unit": "graphs/s", "cores": threads, "kind": "oracle",
+               "sample": f"full oracle runs of the batch's first {done} graphs, {dt:.1f} s"}
+    peak, peak_kind = measured_hbm_peak()
+    step_ms = elapsed_ms / args.steps
+    line = {
+        "metric": BATCH_METRIC, "value": graphs_all / (elapsed_ms * 1e-3), "unit": "graphs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "graphs": count,
+                   "n": n_all, "m": m_all, "mode": args.mode, "k": 8, "tol": 0.05,
+                   "max_iter": 20, "pl_period": 8, "weights": "unit",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "single GPU"
+                   if world == 1 else "replicas"},
+        "one_call_per_graph": {"value": count / (one_ms * 1e-3), "unit": "graphs/s",
+                               "ms": one_ms},
+        "roofline": {"bound": "hbm", "achieved": useful / (step_ms * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": useful / (step_ms * 1e-3) / 1e9 / peak,
+                     "traffic": None, "kernel": "whole batched step (useful sweep bytes: "
+                     "sum over graphs of its iterations x (8 m + 16 n))",
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_graphs_all / (e2e_ms * 1e-3), "unit": "graphs/s",
+                "h2d_bytes_per_step": sum(8 * (g.n + 1) + 4 * g.m for g in gs),
+                "d2h_bytes_per_step": sum(4 * g.n for g in gs), "pinned_host_memory": pin},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "iterations_max": max(iters), "iterations_mean": sum(iters) / len(iters),
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +638,8 @@ def main():
         print("note: the timing rules want at least 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in BATCH_COUNT:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -215,6 +215,39 @@ lpa_status lpa_plan_run(lpa_plan plan, double tol, int32_t max_iter, int32_t* la
 
 lpa_status lpa_plan_destroy(lpa_plan plan);
 
+/* ---- Batched form: many independent graphs in one call. ---------------------------
+ * The graphs are packed into one block-diagonal graph on the device (graph g's vertex
+ * ids shifted by the vertices of the graphs before it; the shift keeps every tie-break
+ * and pick-less decision of the graph alone) and swept together; each graph keeps its
+ * own dN, iteration count and stop test of Alg. 1, and a stopped graph's labels stay
+ * fixed while the others continue.  Results equal one lpa_detect_ex call per graph.
+ * Every pointer in lpa_graph is DEVICE memory owned by the caller; the array of
+ * lpa_graph, stats and changed_out are HOST memory.  The call allocates its packed copy
+ * of the graphs (about 12 B per CSR entry + 40 B per vertex) and frees it before
+ * returning; opt->workspace and opt->labels_in are not used (labels_in must be NULL);
+ * LPA_TIMING and LPA_MODULARITY are ignored; LPA_VALIDATE checks every graph. */
+typedef struct {
+  const int64_t* offsets;  /* device, n + 1 */
+  const int32_t* indices;  /* device, m; 16-byte alignment not required here */
+  const float* weights;    /* device, m, or NULL = unit weights */
+  int32_t n;
+  int64_t m;
+  int32_t* labels_out;     /* device, n: the graph's labels in its own ids */
+} lpa_graph;
+
+typedef struct {
+  int32_t iterations;      /* sweeps the graph took part in */
+  int32_t converged;       /* 1 if its own dN/N < tol stopped it */
+  int64_t edges_scanned;   /* iterations * m, or -1 with LPA_PRUNE (not tracked per graph) */
+} lpa_graph_stats;
+
+/* stats: count entries or NULL; changed_out: count * max_iter entries (graph-major: the
+ * dN of graph g's sweep l at [g * max_iter + l], 0 after it stopped) or NULL.  The total
+ * number of vertices must stay below 2^31 - 16. */
+lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mode, int32_t k,
+                            double tol, int32_t max_iter, const lpa_options* opt,
+                            lpa_graph_stats* stats, int64_t* changed_out);
+
 const char* lpa_status_string(lpa_status s);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* lpa_last_error(void);

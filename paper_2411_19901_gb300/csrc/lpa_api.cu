@@ -596,6 +596,56 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
   return LPA_OK;
 }
 
+// The batched run on a plan over the packed block-diagonal graph: per-graph stop tests
+// (batch_converge), the sweeps skipping stopped graphs, labels unpacked per graph.
+struct BatchCtx {
+  const BatchGraph* gs;  // device table
+  int count;
+  const int32_t* gid;
+  int32_t *gdone, *giter, *gconv, *active;
+  uint32_t* gdn;         // max_iter * count
+  int32_t* labels;       // packed labels, n of the plan
+};
+
+lpa_status batch_run(lpa_plan_s* p, const BatchCtx& b, double tol, int32_t max_iter) {
+  cudaStream_t s = p->stream;
+  const int32_t n = p->n;
+  LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));
+  LPA_CUDA(launch_batch_init(b.gs, b.count, b.gdone, b.giter, b.gconv, b.active, p->st, s));
+  if (n == 0) return LPA_OK;
+  LPA_CUDA(launch_fill_u64(p->dn, 0ull, (int64_t)max_iter * kDnSlots, s));
+  LPA_CUDA(launch_fill_i32((int32_t*)b.gdn, 0, (int64_t)max_iter * b.count, s));
+  LPA_CUDA(launch_init_labels(b.labels, nullptr, n, s));
+  const bool prune = (p->flags & LPA_PRUNE) != 0;
+  uint8_t* act = (uint8_t*)(p->ws + p->lay.act);
+  unsigned long long* scanned = prune ? (unsigned long long*)(p->ws + p->lay.scanned) : nullptr;
+  if (prune) {
+    LPA_CUDA(launch_fill_u8(act, 1, n, s));
+    LPA_CUDA(launch_fill_u64(scanned, 0ull, (int64_t)max_iter * kDnSlots, s));
+  }
+  int32_t* buf[2] = {b.labels, p->tmp};
+  for (int l = 0; l < max_iter; ++l) {
+    const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
+    SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
+                             p->dn + (int64_t)l * kDnSlots, &p->st->done);
+    a.gid = b.gid;
+    a.gdone = b.gdone;
+    a.gdn = b.gdn + (int64_t)l * b.count;
+    if (prune) {
+      a.act_in = act + (int64_t)(l & 1) * n;
+      a.act_out = act + (int64_t)((l + 1) & 1) * n;
+      a.scanned = scanned + (int64_t)l * kDnSlots;
+      LPA_CUDA(launch_fill_u8(a.act_out, 0, n, s));
+    }
+    LPA_CUDA(launch_one_sweep(p, a));
+    LPA_CUDA(launch_batch_converge(b.gs, b.count, a.gdn, b.gdone, b.giter, b.gconv, b.active,
+                                   p->st, l, pick_less, tol, s));
+  }
+  LPA_CUDA(launch_finalize(p->st, b.labels, p->tmp, n, s));
+  LPA_CUDA(launch_unpack_labels(b.gs, b.gid, b.labels, n, s));
+  return LPA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -813,5 +863,125 @@ const char* lpa_last_error(void) { return g_err.c_str(); }
 const char* lpa_version(void) { return "lpa-gb300 0.1 (sm_103a)"; }
 
 uint64_t lpa_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+
+lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mode, int32_t k,
+                            double tol, int32_t max_iter, const lpa_options* opt,
+                            lpa_graph_stats* stats, int64_t* changed_out) {
+  if (count < 0) return fail(LPA_EINVAL, "count = %d is negative", count);
+  if (count > 0 && !graphs) return fail(LPA_EINVAL, "graphs is NULL");
+  if (max_iter < 0 || max_iter > LPA_MAX_ITER)
+    return fail(LPA_EINVAL, "max_iter = %d outside [0, %d]", max_iter, LPA_MAX_ITER);
+  if (!(tol == tol)) return fail(LPA_EINVAL, "tol is NaN");
+  lpa_options o;
+  lpa_options_init(&o);
+  if (opt) o = *opt;
+  if (o.labels_in) return fail(LPA_EINVAL, "labels_in is not supported by lpa_batch_detect");
+  if (count == 0) return LPA_OK;
+  // host: vertex and entry bases of the packed block-diagonal graph
+  std::vector<int64_t> vb(count + 1), eb(count + 1);
+  std::vector<BatchGraph> tab(count);
+  bool weighted = false;
+  for (int g = 0; g < count; ++g) {
+    const lpa_graph& G = graphs[g];
+    lpa_status cs = check_graph_args(G.offsets, G.indices, G.n, G.m);
+    if (cs != LPA_OK) return fail(cs, "graph %d: %s", g, lpa_last_error());
+    if (G.n > 0 && !G.labels_out) return fail(LPA_EINVAL, "graph %d: labels_out is NULL", g);
+    tab[g] = BatchGraph{G.offsets, G.indices, G.weights, G.labels_out, vb[g], eb[g], G.m, G.n, 0};
+    vb[g + 1] = vb[g] + G.n;
+    eb[g + 1] = eb[g] + G.m;
+    weighted = weighted || (G.weights != nullptr && G.m > 0);
+  }
+  const int64_t N = vb[count], M = eb[count];
+  if (N > 0x7ffffff0LL) return fail(LPA_EUNSUPPORTED, "batch of %lld vertices exceeds int32 ids", (long long)N);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // one device block: table, bases, packed CSR, graph ids, per-graph state, packed labels
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = at;
+    at = align256(at + bytes);
+    return r;
+  };
+  const size_t o_tab = take(sizeof(BatchGraph) * count), o_vb = take(8 * (size_t)(count + 1)),
+               o_eb = take(8 * (size_t)(count + 1)), o_off = take(8 * (size_t)(N + 1)),
+               o_idx = take(4 * (size_t)M), o_w = weighted ? take(4 * (size_t)M) : 0,
+               o_gid = take(4 * (size_t)N), o_state = take(4 * (3 * (size_t)count + 2)),
+               o_gdn = take(4 * (size_t)max_iter * count + 4), o_lab = take(4 * (size_t)N + 4);
+  char* dev = nullptr;
+  LPA_CUDA(cudaMallocAsync((void**)&dev, at, s));
+  auto cleanup = [&](lpa_status st) {
+    cudaFreeAsync(dev, s);
+    cudaStreamSynchronize(s);
+    return st;
+  };
+  BatchGraph* d_tab = (BatchGraph*)(dev + o_tab);
+  int64_t* d_off = (int64_t*)(dev + o_off);
+  int32_t* d_idx = (int32_t*)(dev + o_idx);
+  float* d_w = weighted ? (float*)(dev + o_w) : nullptr;
+  int32_t* d_gid = (int32_t*)(dev + o_gid);
+  int32_t* d_state = (int32_t*)(dev + o_state);  // gdone, giter, gconv, active, err
+  BatchCtx b{d_tab, count, d_gid, d_state, d_state + count, d_state + 2 * count,
+             d_state + 3 * count, (uint32_t*)(dev + o_gdn), (int32_t*)(dev + o_lab)};
+  int32_t* d_err = d_state + 3 * count + 1;
+  cudaError_t ce = cudaMemcpyAsync(d_tab, tab.data(), sizeof(BatchGraph) * count,
+                                   cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(dev + o_vb, vb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(dev + o_eb, eb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(d_off + N, &M, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = launch_fill_i32(d_err, 0, 1, s);
+  const bool validate = (o.flags & LPA_VALIDATE) != 0;
+  if (ce == cudaSuccess)
+    ce = launch_pack_batch(d_tab, (const int64_t*)(dev + o_vb), (const int64_t*)(dev + o_eb),
+                           count, N, M, d_off, d_idx, d_w, d_gid, validate, d_err, s);
+  if (ce != cudaSuccess)
+    return cleanup(fail(LPA_ECUDA, "batch packing: %s", cudaGetErrorString(ce)));
+  if (validate) {
+    int32_t err = 0;
+    ce = cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cleanup(fail(LPA_ECUDA, "batch validation: %s", cudaGetErrorString(ce)));
+    if (err)
+      return cleanup(fail(LPA_EINVAL, "invalid input in the batch:%s%s%s",
+                          (err & kErrOffsets) ? " offsets" : "",
+                          (err & kErrIndex) ? " index out of range" : "",
+                          (err & kErrWeight) ? " negative/non-finite weight" : ""));
+  }
+  lpa_options po = o;
+  po.flags &= ~(LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY);
+  po.workspace = nullptr;
+  po.workspace_bytes = 0;
+  lpa_plan_s* p = nullptr;
+  lpa_status st = plan_create(d_off, d_idx, d_w, (int32_t)N, M, mode, k, &po, &p);
+  if (st != LPA_OK) return cleanup(st);
+  st = batch_run(p, b, tol, max_iter);
+  std::vector<int32_t> h_state(3 * (size_t)count);
+  std::vector<uint32_t> h_gdn((size_t)max_iter * count);
+  if (st == LPA_OK) {
+    ce = cudaMemcpyAsync(h_state.data(), d_state, 4 * 3 * (size_t)count, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && changed_out && max_iter > 0)
+      ce = cudaMemcpyAsync(h_gdn.data(), b.gdn, 4 * (size_t)max_iter * count,
+                           cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) st = fail(LPA_ECUDA, "batch results: %s", cudaGetErrorString(ce));
+  }
+  destroy_plan(p);
+  if (st != LPA_OK) return cleanup(st);
+  const bool prune = (o.flags & LPA_PRUNE) != 0;
+  for (int g = 0; g < count; ++g) {
+    const int32_t it = h_state[(size_t)count + g];
+    if (stats) {
+      stats[g].iterations = it;
+      stats[g].converged = h_state[2 * (size_t)count + g];
+      stats[g].edges_scanned = prune ? -1 : (int64_t)it * graphs[g].m;
+    }
+    if (changed_out)
+      for (int l = 0; l < max_iter; ++l)
+        changed_out[(size_t)g * max_iter + l] = l < it ? (int64_t)h_gdn[(size_t)l * count + g] : 0;
+  }
+  return cleanup(LPA_OK);
+}
 
 }  // extern "C"

@@ -37,8 +37,8 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
   const int v = a.hubs[h];
   const int64_t base = a.off[v];
   const int64_t d = a.off[v + 1] - base;
-  if (a.act_in != nullptr && !a.act_in[v]) {  // not marked unprocessed: keep the label
-    if (tid == 0) a.c_next[v] = a.c_prev[v];
+  if ((a.act_in != nullptr && !a.act_in[v]) || (a.gid != nullptr && a.gdone[a.gid[v]])) {
+    if (tid == 0) a.c_next[v] = a.c_prev[v];  // not swept: keep the label
     return;
   }
   int lg = 1;
@@ -102,6 +102,7 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
     a.c_next[v] = nl;
     s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn, 1ull);
+    if (nl != own && a.gdn != nullptr) atomicAdd(a.gdn + a.gid[v], 1u);
     if (a.scanned) atomicAdd(a.scanned + (h & (kDnSlots - 1)), (unsigned long long)d);
   }
   if (a.act_out != nullptr) {  // a moved vertex marks its neighbours unprocessed
@@ -141,7 +142,8 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
   __syncthreads();
   int changed = 0;
   int nl = 0;
-  const bool act = tid < nv && (a.act_in == nullptr || a.act_in[v0 + tid] != 0);
+  const bool act = tid < nv && (a.act_in == nullptr || a.act_in[v0 + tid] != 0) &&
+                   (a.gid == nullptr || !a.gdone[a.gid[v0 + tid]]);
   if (tid < nv) {
     const int b = s_start[tid], d = act ? s_start[tid + 1] - b : 0;
     int best = -1;
@@ -174,6 +176,7 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
     nl = commit(best, s_old[tid], a.pick_less);
     changed = nl != s_old[tid];
     a.c_next[v0 + tid] = nl;
+    if (changed && a.gdn != nullptr) atomicAdd(a.gdn + a.gid[v0 + tid], 1u);
   }
   const int cnt = __syncthreads_count(changed);
   if (tid == 0 && cnt > 0) atomicAdd(a.dn, (unsigned long long)cnt);

@@ -122,12 +122,31 @@ struct SweepArgs {
   const uint8_t* act_in;
   uint8_t* act_out;
   unsigned long long* scanned;
+  // Batched form, null otherwise: vertex v belongs to graph gid[v]; a graph with
+  // gdone[g] != 0 has stopped (its vertices keep their labels); gdn[g] counts the
+  // graph's changed labels of this sweep.
+  const int32_t* gid;
+  const int32_t* gdone;
+  uint32_t* gdn;
   int32_t nchunks;
   int32_t nhubs;
   int32_t pick_less;
   int32_t e0;
   int32_t lmax;
   int64_t m;
+};
+
+// One graph of a batch (device table): its caller arrays, output, and its vertex and
+// CSR-entry bases in the packed block-diagonal graph.
+struct BatchGraph {
+  const int64_t* off;
+  const int32_t* idx;
+  const float* w;   // null: unit weights
+  int32_t* out;     // labels_out of the graph
+  int64_t vb, eb;
+  int64_t m;
+  int32_t n;
+  int32_t pad;
 };
 
 // Arguments of the degree binning.
@@ -216,6 +235,18 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const floa
 int modularity_partials(int32_t n);
 
 inline int64_t num_segments(int64_t n) { return (n + kSegment - 1) / kSegment; }
+
+// Batched form (lpa_batch.cu).  vb / eb: count + 1 ascending vertex / entry bases.
+cudaError_t launch_pack_batch(const BatchGraph* gs, const int64_t* vb, const int64_t* eb, int count,
+                              int64_t nv, int64_t ne, int64_t* off, int32_t* idx, float* w,
+                              int32_t* gid, bool validate, int32_t* err, cudaStream_t s);
+cudaError_t launch_batch_init(const BatchGraph* gs, int count, int32_t* gdone, int32_t* giter,
+                              int32_t* gconv, int32_t* active, DevState* st, cudaStream_t s);
+cudaError_t launch_batch_converge(const BatchGraph* gs, int count, const uint32_t* gdn_l,
+                                  int32_t* gdone, int32_t* giter, int32_t* gconv, int32_t* active,
+                                  DevState* st, int l, int pick_less, double tol, cudaStream_t s);
+cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const int32_t* c,
+                                 int64_t nv, cudaStream_t s);
 
 // Record the message returned by lpa_last_error() on this host thread; returns s.
 int set_last_error(int s, const char* msg);

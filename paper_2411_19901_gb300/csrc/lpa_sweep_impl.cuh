@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   const int64_t base = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
   const int64_t d = h.w;
   const int L = leaf_count(d, a.e0, a.lmax);
-  if (a.act_in != nullptr && !a.act_in[v]) {  // not marked unprocessed: keep the label
-    if (tid == 0) a.c_next[v] = a.c_prev[v];
+  if ((a.act_in != nullptr && !a.act_in[v]) || (a.gid != nullptr && a.gdone[a.gid[v]])) {
+    if (tid == 0) a.c_next[v] = a.c_prev[v];  // not swept: keep the label
     return;
   }
   const int own = a.c_prev[v];
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
     a.c_next[v] = nl;
     s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn + (blockIdx.x & (kDnSlots - 1)), 1ull);
+    if (nl != own && a.gdn != nullptr) atomicAdd(a.gdn + a.gid[v], 1u);
     if (a.scanned) atomicAdd(a.scanned + (blockIdx.x & (kDnSlots - 1)), (unsigned long long)d);
   }
   if (a.act_out != nullptr) {  // a moved vertex marks its neighbours unprocessed
@@ -153,7 +154,9 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
     leaf = (l.w >> kLaneLeafShift) & 31;
     L = 1 << (l.w >> kLaneLgShift);
   }
-  const bool act = v >= 0 && (a.act_in == nullptr || a.act_in[v] != 0);
+  const int g = (v >= 0 && a.gid != nullptr) ? a.gid[v] : -1;
+  const bool act = v >= 0 && (a.act_in == nullptr || a.act_in[v] != 0) &&
+                   (g < 0 || !a.gdone[g]);
   S st;
   int own = -1;
   if (v >= 0) {
@@ -197,6 +200,10 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
   const int wsum = __reduce_add_sync(kFullMask, changed);
   if (lane == 0 && wsum > 0)
     atomicAdd(a.dn + ((q >> 5) & (kDnSlots - 1)), (unsigned long long)wsum);
+  if (a.gdn != nullptr && wsum > 0) {  // batched: one atomic per graph present in the warp
+    const unsigned same = __match_any_sync(kFullMask, changed ? g : -1 - lane);
+    if (changed && lane == __ffs(same) - 1) atomicAdd(a.gdn + g, (unsigned)__popc(same));
+  }
   if (a.act_out != nullptr) {
     // the vertex's leader knows whether it moved; each of its lanes marks its own leaf
     const int moved = __shfl_sync(kFullMask, changed, lane - leaf);

@@ -74,6 +74,25 @@ class lpa_stats(ctypes.Structure):
         }
 
 
+class lpa_graph(ctypes.Structure):
+    _fields_ = [
+        ("offsets", ctypes.c_void_p),
+        ("indices", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p),
+        ("n", ctypes.c_int32),
+        ("m", ctypes.c_int64),
+        ("labels_out", ctypes.c_void_p),
+    ]
+
+
+class lpa_graph_stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("edges_scanned", ctypes.c_int64),
+    ]
+
+
 class lpa_options(ctypes.Structure):
     _fields_ = [
         ("pl_period", ctypes.c_int32),
@@ -108,6 +127,8 @@ _SIG = {
     "lpa_workspace_size_ex": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                                 ctypes.c_int32, _P]),
     "lpa_modularity_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "lpa_batch_detect": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
     "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "lpa_plan_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
@@ -341,6 +362,29 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def lpa_batch_detect(graphs, mode="mg", k=8, tol=0.05, max_iter=20,
+                     opt: lpa_options | None = None):
+    """Batched form.  ``graphs``: sequence of (offsets, indices, weights|None, labels_out)
+    device tensors.  Returns (list of per-graph stat dicts, changed array [count, max_iter])."""
+    import numpy as np
+
+    count = len(graphs)
+    arr = (lpa_graph * max(count, 1))()
+    for g, (off, idx, w, out) in enumerate(graphs):
+        arr[g] = lpa_graph(_ptr(off), _ptr(idx), _ptr(w), int(off.numel() - 1),
+                           int(idx.numel()), _ptr(out))
+    stats = (lpa_graph_stats * max(count, 1))()
+    changed = np.zeros((max(count, 1), max(max_iter, 1)), dtype=np.int64)
+    _check(load().lpa_batch_detect(ctypes.cast(arr, ctypes.c_void_p), count, _mode(mode), k,
+                                   tol, max_iter,
+                                   ctypes.byref(opt) if opt is not None else None,
+                                   ctypes.cast(stats, ctypes.c_void_p),
+                                   changed.ctypes.data))
+    out = [{"iterations": int(stats[g].iterations), "converged": bool(stats[g].converged),
+            "edges_scanned": int(stats[g].edges_scanned)} for g in range(count)]
+    return out, changed[:count, :max_iter]
 
 
 def detect(offsets, indices, weights=None, mode="mg", k=8, tol=0.05, max_iter=20,
