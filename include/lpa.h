@@ -248,6 +248,36 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
                             double tol, int32_t max_iter, const lpa_options* opt,
                             lpa_graph_stats* stats, int64_t* changed_out);
 
+/* ---- Served form: continuous batching of label-propagation requests. ---------------
+ * A server owns a set of resident graphs, packed block-diagonally as in lpa_batch_detect.
+ * lpa_server_submit queues a request (the graph's device arrays must stay valid, and
+ * labels_out untouched, until lpa_server_poll reports it done); every lpa_server_step
+ * first admits queued requests in arrival order while the resident graphs' HBM
+ * footprint (packed CSR, labels and descriptors: about 8(n+1) + 8m + 44n + 16m/e0
+ * bytes each) fits hbm_budget_bytes (0 = no limit; one request is always admitted when
+ * none is resident), then runs one sweep of every resident graph -- each at its own
+ * iteration, with its own pick-less setting and stop test (Alg. 1) -- and writes the
+ * labels of the graphs that stopped.  A request's result equals lpa_detect_ex on its
+ * graph alone, whatever else is resident.  One host thread drives a server; calls are
+ * ordered on opt->stream and each step synchronises it once.  LPA_PRUNE and labels_in
+ * are not supported; LPA_VALIDATE checks each graph at submission. */
+typedef struct lpa_server_s* lpa_server;
+
+lpa_status lpa_server_create(lpa_mode mode, int32_t k, double tol, int32_t max_iter,
+                             size_t hbm_budget_bytes, const lpa_options* opt,
+                             lpa_server* server_out);
+/* graph: HOST struct of device pointers; ticket (host) identifies the request.  A graph
+ * larger than the budget is refused (LPA_EINVAL). */
+lpa_status lpa_server_submit(lpa_server server, const lpa_graph* graph, uint64_t* ticket);
+/* pending_out (host, may be NULL): requests resident or queued after the step. */
+lpa_status lpa_server_step(lpa_server server, int32_t* pending_out);
+/* done (host) = 1 once the request's labels are written; stats (host, may be NULL) as in
+ * lpa_batch_detect.  A ticket reported done is forgotten (later polls: LPA_EINVAL). */
+lpa_status lpa_server_poll(lpa_server server, uint64_t ticket, int32_t* done,
+                           lpa_graph_stats* stats);
+/* Frees the server; requests not yet done are dropped (their outputs unspecified). */
+lpa_status lpa_server_destroy(lpa_server server);
+
 const char* lpa_status_string(lpa_status s);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* lpa_last_error(void);

@@ -11,7 +11,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/lpa.h"
@@ -646,6 +648,228 @@ lpa_status batch_run(lpa_plan_s* p, const BatchCtx& b, double tol, int32_t max_i
   return LPA_OK;
 }
 
+// ------------------------------------------------------------------ served form
+
+// One request of a server: the caller's graph (device arrays that must stay valid until
+// the request is reported done) and its progress.
+struct ServeReq {
+  uint64_t ticket = 0;
+  lpa_graph g{};
+  size_t foot = 0;
+  int32_t state = 0;  // 0 waiting, 1 resident, 2 done
+  int32_t iterations = 0, converged = 0;
+  int64_t vb = -1;    // vertex base in the current packing while resident
+};
+
+// The resident graphs packed block-diagonally, their per-graph state and the plan over
+// the packed graph.  Rebuilt whenever the resident set changes; labels carry over.
+struct Packing {
+  char* dev = nullptr;
+  int count = 0;
+  int64_t N = 0, M = 0;
+  BatchGraph* tab = nullptr;
+  int64_t *vb = nullptr, *eb = nullptr, *off = nullptr, *old_vb = nullptr;
+  int32_t* idx = nullptr;
+  float* w = nullptr;
+  int32_t* gid = nullptr;
+  int32_t *gdone = nullptr, *giter = nullptr, *gconv = nullptr, *gpl = nullptr, *gfin = nullptr;
+  uint32_t* gdn = nullptr;
+  int32_t* lab[2] = {nullptr, nullptr};
+  int cur = 0;
+  lpa_plan_s* plan = nullptr;
+};
+
+// HBM a resident graph takes: packed CSR (8 B offset + 4 B index (+ 4 B weight) per entry),
+// graph id and two labels per vertex, and the plan's vertex and lane descriptors.
+size_t serve_footprint(const lpa_graph& g, int e0) {
+  const size_t n = (size_t)g.n, m = (size_t)g.m;
+  return 8 * (n + 1) + 8 * m + 12 * n + 32 * n + 16 * (m / (size_t)e0 + 32) + 1024;
+}
+
+}  // namespace
+
+struct lpa_server_s {
+  int mode = kMG, k = 8;
+  double tol = 0.05;
+  int max_iter = 20;
+  lpa_options opt{};
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  uint64_t next = 1;
+  std::deque<ServeReq*> waiting;
+  std::vector<ServeReq*> resident;
+  std::unordered_map<uint64_t, ServeReq*> reqs;
+  Packing pk;
+  bool dirty = false;
+  int32_t* d_err = nullptr;      // validation scratch
+  int32_t* h_state = nullptr;    // page-locked: gfin, giter, gconv of the last step
+  size_t h_state_cap = 0;
+};
+
+namespace {
+
+void free_packing(Packing& P, cudaStream_t s) {
+  if (P.plan) destroy_plan(P.plan);
+  if (P.dev) cudaFreeAsync(P.dev, s);
+  P = Packing{};
+}
+
+lpa_status serve_repack(lpa_server_s* S) {
+  cudaStream_t s = S->stream;
+  const int count = (int)S->resident.size();
+  std::vector<int64_t> vb(count + 1, 0), eb(count + 1, 0), old_vb(count);
+  std::vector<BatchGraph> tab(count);
+  std::vector<int32_t> st(5 * (size_t)count, 0);  // gdone, giter, gconv, gpl, gfin
+  bool weighted = false;
+  const int rho = S->opt.pl_period;
+  for (int g = 0; g < count; ++g) {
+    ServeReq* r = S->resident[g];
+    tab[g] = BatchGraph{r->g.offsets, r->g.indices, r->g.weights, r->g.labels_out, vb[g], eb[g],
+                        r->g.m, r->g.n, 0};
+    old_vb[g] = r->vb;
+    vb[g + 1] = vb[g] + r->g.n;
+    eb[g + 1] = eb[g] + r->g.m;
+    weighted = weighted || (r->g.weights && r->g.m > 0);
+    st[(size_t)count + g] = r->iterations;
+    st[3 * (size_t)count + g] = (rho > 0 && r->iterations % rho == 0) ? 1 : 0;
+  }
+  const int64_t N = vb[count], M = eb[count];
+  if (N > 0x7ffffff0LL) return fail(LPA_EUNSUPPORTED, "resident vertices exceed int32 ids");
+  Packing P;
+  P.count = count;
+  P.N = N;
+  P.M = M;
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = at;
+    at = align256(at + bytes);
+    return r;
+  };
+  const size_t o_tab = take(sizeof(BatchGraph) * count), o_vb = take(8 * (size_t)(count + 1)),
+               o_eb = take(8 * (size_t)(count + 1)), o_ovb = take(8 * (size_t)count),
+               o_off = take(8 * (size_t)(N + 1)), o_idx = take(4 * (size_t)M + 4),
+               o_w = weighted ? take(4 * (size_t)M + 4) : 0, o_gid = take(4 * (size_t)N + 4),
+               o_st = take(4 * 5 * (size_t)count), o_gdn = take(4 * (size_t)count),
+               o_l0 = take(4 * (size_t)N + 4), o_l1 = take(4 * (size_t)N + 4);
+  LPA_CUDA(cudaMallocAsync((void**)&P.dev, at, s));
+  P.tab = (BatchGraph*)(P.dev + o_tab);
+  P.vb = (int64_t*)(P.dev + o_vb);
+  P.eb = (int64_t*)(P.dev + o_eb);
+  P.old_vb = (int64_t*)(P.dev + o_ovb);
+  P.off = (int64_t*)(P.dev + o_off);
+  P.idx = (int32_t*)(P.dev + o_idx);
+  P.w = weighted ? (float*)(P.dev + o_w) : nullptr;
+  P.gid = (int32_t*)(P.dev + o_gid);
+  int32_t* d_st = (int32_t*)(P.dev + o_st);
+  P.gdone = d_st;
+  P.giter = d_st + count;
+  P.gconv = d_st + 2 * count;
+  P.gpl = d_st + 3 * count;
+  P.gfin = d_st + 4 * count;
+  P.gdn = (uint32_t*)(P.dev + o_gdn);
+  P.lab[0] = (int32_t*)(P.dev + o_l0);
+  P.lab[1] = (int32_t*)(P.dev + o_l1);
+  cudaError_t ce = cudaMemcpyAsync(P.tab, tab.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.vb, vb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.eb, eb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.old_vb, old_vb.data(), 8 * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_st, st.data(), 4 * 5 * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.off + N, &M, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = launch_pack_batch(P.tab, P.vb, P.eb, count, N, M, P.off, P.idx, P.w, P.gid, false, nullptr, s);
+  if (ce == cudaSuccess)
+    ce = launch_carry_labels(P.tab, P.old_vb, P.gid, S->pk.lab[S->pk.cur], P.lab[0], N, s);
+  // host vectors must outlive the pageable copies: wait for them before returning
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    cudaFreeAsync(P.dev, s);
+    return fail(LPA_ECUDA, "server repack: %s", cudaGetErrorString(ce));
+  }
+  lpa_options po = S->opt;
+  po.flags &= ~(LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY | LPA_PRUNE);
+  po.workspace = nullptr;
+  po.workspace_bytes = 0;
+  po.labels_in = nullptr;
+  lpa_status rs = plan_create(P.off, P.idx, P.w, (int32_t)N, M, (lpa_mode)S->mode, S->k, &po, &P.plan);
+  if (rs != LPA_OK) {
+    cudaFreeAsync(P.dev, s);
+    return rs;
+  }
+  free_packing(S->pk, s);
+  S->pk = P;
+  for (int g = 0; g < count; ++g) S->resident[g]->vb = vb[g];
+  return LPA_OK;
+}
+
+lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
+  cudaStream_t s = S->stream;
+  while (!S->waiting.empty()) {  // admission by HBM footprint, first come first served
+    ServeReq* r = S->waiting.front();
+    if (S->budget && S->used + r->foot > S->budget && !S->resident.empty()) break;
+    S->waiting.pop_front();
+    r->state = 1;
+    r->vb = -1;
+    S->resident.push_back(r);
+    S->used += r->foot;
+    S->dirty = true;
+  }
+  if (S->resident.empty()) {
+    if (pending_out) *pending_out = (int32_t)S->waiting.size();
+    return LPA_OK;
+  }
+  if (S->dirty) {
+    lpa_status rs = serve_repack(S);
+    if (rs != LPA_OK) return rs;
+    S->dirty = false;
+  }
+  Packing& P = S->pk;
+  LPA_CUDA(launch_fill_i32((int32_t*)P.gdn, 0, P.count, s));
+  LPA_CUDA(launch_fill_i32(P.gfin, 0, P.count, s));
+  SweepArgs a = sweep_args(P.plan, P.lab[P.cur], P.lab[1 - P.cur], 0, P.plan->dn, nullptr);
+  a.gid = P.gid;
+  a.gdone = P.gdone;
+  a.gdn = P.gdn;
+  a.gpl = P.gpl;
+  LPA_CUDA(launch_one_sweep(P.plan, a));
+  LPA_CUDA(launch_serve_converge(P.tab, P.count, P.gdn, P.gdone, P.giter, P.gconv, P.gpl, P.gfin,
+                                 S->max_iter, S->opt.pl_period, S->tol, s));
+  P.cur ^= 1;
+  LPA_CUDA(launch_unpack_finished(P.tab, P.gid, P.gfin, P.lab[P.cur], P.N, s));
+  if (S->h_state_cap < 3 * (size_t)P.count) {
+    if (S->h_state) cudaFreeHost(S->h_state);
+    S->h_state = nullptr;
+    S->h_state_cap = 0;
+    LPA_CUDA(cudaMallocHost((void**)&S->h_state, 4 * 3 * (size_t)P.count));
+    S->h_state_cap = 3 * (size_t)P.count;
+  }
+  // giter, gconv are adjacent in the state block; gfin follows gpl
+  LPA_CUDA(cudaMemcpyAsync(S->h_state, P.giter, 4 * 2 * (size_t)P.count, cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(S->h_state + 2 * P.count, P.gfin, 4 * (size_t)P.count,
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaStreamSynchronize(s));
+  std::vector<ServeReq*> keep;
+  keep.reserve(S->resident.size());
+  for (int g = 0; g < P.count; ++g) {
+    ServeReq* r = S->resident[g];
+    r->iterations = S->h_state[g];
+    if (S->h_state[2 * P.count + g]) {
+      r->state = 2;
+      r->converged = S->h_state[P.count + g];
+      r->vb = -1;
+      S->used -= r->foot;
+      S->dirty = true;
+    } else {
+      keep.push_back(r);
+    }
+  }
+  if (S->dirty) {
+    // the next packing carries labels by each graph's base in this one
+    S->resident.swap(keep);
+  }
+  if (pending_out) *pending_out = (int32_t)(S->resident.size() + S->waiting.size());
+  return LPA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -982,6 +1206,118 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
         changed_out[(size_t)g * max_iter + l] = l < it ? (int64_t)h_gdn[(size_t)l * count + g] : 0;
   }
   return cleanup(LPA_OK);
+}
+
+
+lpa_status lpa_server_create(lpa_mode mode, int32_t k, double tol, int32_t max_iter,
+                             size_t hbm_budget_bytes, const lpa_options* opt, lpa_server* out) {
+  if (!out) return fail(LPA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (mode != LPA_EXACT && mode != LPA_MG && mode != LPA_BM)
+    return fail(LPA_EINVAL, "unknown mode %d", (int)mode);
+  if (mode == LPA_MG && !valid_k(k)) return fail(LPA_EUNSUPPORTED, "k = %d is not built", k);
+  if (max_iter < 0 || max_iter > LPA_MAX_ITER)
+    return fail(LPA_EINVAL, "max_iter = %d outside [0, %d]", max_iter, LPA_MAX_ITER);
+  if (!(tol == tol)) return fail(LPA_EINVAL, "tol is NaN");
+  lpa_options o;
+  lpa_options_init(&o);
+  if (opt) o = *opt;
+  if (o.flags & LPA_PRUNE) return fail(LPA_EUNSUPPORTED, "LPA_PRUNE is not supported by the server");
+  if (o.labels_in) return fail(LPA_EINVAL, "labels_in is not supported by the server");
+  if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
+  if ((o.flags & (LPA_MG_UNCLAMPED | LPA_RESCAN)) && mode != LPA_MG)
+    return fail(LPA_EINVAL, "LPA_MG_UNCLAMPED and LPA_RESCAN apply to LPA_MG only");
+  lpa_server_s* S = new lpa_server_s();
+  S->mode = (int)mode;
+  S->k = mode == LPA_MG ? k : 1;
+  S->tol = tol;
+  S->max_iter = max_iter;
+  S->opt = o;
+  S->stream = (cudaStream_t)o.stream;
+  S->budget = hbm_budget_bytes;
+  cudaError_t ce = cudaMallocAsync((void**)&S->d_err, 256, S->stream);
+  if (ce != cudaSuccess) {
+    delete S;
+    return fail(LPA_ENOMEM, "server scratch: %s", cudaGetErrorString(ce));
+  }
+  *out = S;
+  return LPA_OK;
+}
+
+lpa_status lpa_server_submit(lpa_server S, const lpa_graph* graph, uint64_t* ticket) {
+  if (!S || !graph || !ticket) return fail(LPA_EINVAL, "NULL argument");
+  const lpa_graph& g = *graph;
+  lpa_status cs = check_graph_args(g.offsets, g.indices, g.n, g.m);
+  if (cs != LPA_OK) return cs;
+  if (g.n > 0 && !g.labels_out) return fail(LPA_EINVAL, "labels_out is NULL");
+  const size_t foot = serve_footprint(g, S->opt.leaf_e0);
+  if (S->budget && foot > S->budget)
+    return fail(LPA_EINVAL, "graph needs %zu bytes, the server's budget is %zu", foot, S->budget);
+  if ((S->opt.flags & LPA_VALIDATE) && g.n > 0) {
+    int32_t err = 0;
+    cudaError_t ce = launch_fill_i32(S->d_err, 0, 1, S->stream);
+    if (ce == cudaSuccess)
+      ce = launch_validate(g.offsets, g.indices, g.weights, g.n, g.m, nullptr, S->d_err, S->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&err, S->d_err, 4, cudaMemcpyDeviceToHost, S->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(S->stream);
+    if (ce != cudaSuccess) return fail(LPA_ECUDA, "validation: %s", cudaGetErrorString(ce));
+    if (err) return fail(LPA_EINVAL, "invalid graph (error bits %d)", err);
+  }
+  ServeReq* r = new ServeReq();
+  r->ticket = S->next++;
+  r->g = g;
+  r->foot = foot;
+  if (g.n == 0 || S->max_iter == 0) {  // nothing to sweep
+    r->state = 2;
+    r->converged = g.n == 0;
+    if (g.n > 0) {  // max_iter = 0: the initial labels C[i] = i
+      cudaError_t ce = launch_init_labels(g.labels_out, nullptr, g.n, S->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(S->stream);
+      if (ce != cudaSuccess) {
+        delete r;
+        return fail(LPA_ECUDA, "init: %s", cudaGetErrorString(ce));
+      }
+    }
+  } else {
+    S->waiting.push_back(r);
+  }
+  S->reqs[r->ticket] = r;
+  *ticket = r->ticket;
+  return LPA_OK;
+}
+
+lpa_status lpa_server_step(lpa_server S, int32_t* pending_out) {
+  if (!S) return fail(LPA_EINVAL, "server is NULL");
+  return serve_step(S, pending_out);
+}
+
+lpa_status lpa_server_poll(lpa_server S, uint64_t ticket, int32_t* done, lpa_graph_stats* stats) {
+  if (!S || !done) return fail(LPA_EINVAL, "NULL argument");
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(LPA_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  ServeReq* r = it->second;
+  *done = r->state == 2;
+  if (stats) {
+    stats->iterations = r->iterations;
+    stats->converged = r->converged;
+    stats->edges_scanned = (int64_t)r->iterations * r->g.m;
+  }
+  if (r->state == 2) {
+    S->reqs.erase(it);
+    delete r;
+  }
+  return LPA_OK;
+}
+
+lpa_status lpa_server_destroy(lpa_server S) {
+  if (!S) return LPA_OK;
+  free_packing(S->pk, S->stream);
+  if (S->d_err) cudaFreeAsync(S->d_err, S->stream);
+  cudaStreamSynchronize(S->stream);
+  if (S->h_state) cudaFreeHost(S->h_state);
+  for (auto& kv : S->reqs) delete kv.second;
+  delete S;
+  return LPA_OK;
 }
 
 }  // extern "C"

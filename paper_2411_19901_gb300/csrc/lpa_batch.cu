@@ -127,6 +127,53 @@ __global__ void unpack_labels_kernel(const BatchGraph* __restrict__ gs, const in
   }
 }
 
+// Served form, after one sweep of every resident graph: graph g counts its sweep, applies
+// its own stop test (its own pick-less setting and iteration number, Alg. 1) or stops at
+// max_iter, and sets its pick-less flag for its next sweep.  gfin marks the graphs that
+// stopped in this sweep.
+__global__ void serve_converge_kernel(const BatchGraph* __restrict__ gs, int count,
+                                      const uint32_t* __restrict__ gdn, int32_t* gdone,
+                                      int32_t* giter, int32_t* gconv, int32_t* gpl, int32_t* gfin,
+                                      int max_iter, int rho, double tol) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count || gdone[g]) return;
+  const int l = giter[g];  // sweeps done before this one
+  giter[g] = l + 1;
+  const bool stop = !gpl[g] && (double)gdn[g] / (double)gs[g].n < tol;
+  if (stop || l + 1 >= max_iter) {
+    gdone[g] = 1;
+    gconv[g] = stop;
+    gfin[g] = 1;
+  }
+  gpl[g] = (rho > 0 && (l + 1) % rho == 0) ? 1 : 0;
+}
+
+// New packing of the resident graphs: a graph that was resident before (old_vb[g] >= 0)
+// carries its labels over, shifted to its new base; a new graph starts from C[i] = i.
+__global__ void carry_labels_kernel(const BatchGraph* __restrict__ gs,
+                                    const int64_t* __restrict__ old_vb, const int32_t* __restrict__ gid,
+                                    const int32_t* __restrict__ c_old, int32_t* c_new, int64_t nv) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int g = gid[v];
+    const int64_t ob = old_vb[g], nb = gs[g].vb;
+    c_new[v] = ob < 0 ? (int32_t)v : (int32_t)(c_old[ob + (v - nb)] - ob + nb);
+  }
+}
+
+// Labels of the graphs that stopped in this sweep back to their own outputs.
+__global__ void unpack_finished_kernel(const BatchGraph* __restrict__ gs, const int32_t* __restrict__ gid,
+                                       const int32_t* __restrict__ gfin, const int32_t* __restrict__ c,
+                                       int64_t nv) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int g = gid[v];
+    if (!gfin[g]) continue;
+    const BatchGraph G = gs[g];
+    G.out[v - G.vb] = (int32_t)(c[v] - G.vb);
+  }
+}
+
 inline unsigned grid_of(int64_t n) {
   const int64_t g = (n + 255) / 256;
   return (unsigned)(g < 152 * 32 ? (g > 0 ? g : 1) : 152 * 32);
@@ -168,6 +215,33 @@ cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const
                                  int64_t nv, cudaStream_t s) {
   if (nv == 0) return cudaSuccess;
   unpack_labels_kernel<<<grid_of(nv), 256, 0, s>>>(gs, gid, c, nv);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_serve_converge(const BatchGraph* gs, int count, const uint32_t* gdn,
+                                  int32_t* gdone, int32_t* giter, int32_t* gconv, int32_t* gpl,
+                                  int32_t* gfin, int max_iter, int rho, double tol,
+                                  cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  serve_converge_kernel<<<(count + 255) / 256, 256, 0, s>>>(gs, count, gdn, gdone, giter, gconv,
+                                                             gpl, gfin, max_iter, rho, tol);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_carry_labels(const BatchGraph* gs, const int64_t* old_vb, const int32_t* gid,
+                                const int32_t* c_old, int32_t* c_new, int64_t nv, cudaStream_t s) {
+  if (nv == 0) return cudaSuccess;
+  carry_labels_kernel<<<grid_of(nv), 256, 0, s>>>(gs, old_vb, gid, c_old, c_new, nv);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_finished(const BatchGraph* gs, const int32_t* gid, const int32_t* gfin,
+                                   const int32_t* c, int64_t nv, cudaStream_t s) {
+  if (nv == 0) return cudaSuccess;
+  unpack_finished_kernel<<<grid_of(nv), 256, 0, s>>>(gs, gid, gfin, c, nv);
   count_launch();
   return cudaGetLastError();
 }

@@ -98,7 +98,7 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
         bk = s_bk[w];
       }
     const int own = a.c_prev[v];
-    const int nl = commit(bv > 0.f ? bk : -1, own, a.pick_less);
+    const int nl = commit(bv > 0.f ? bk : -1, own, a.gpl != nullptr ? a.gpl[a.gid[v]] : a.pick_less);
     a.c_next[v] = nl;
     s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn, 1ull);
@@ -173,7 +173,7 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
           best = tk[s];
         }
     }
-    nl = commit(best, s_old[tid], a.pick_less);
+    nl = commit(best, s_old[tid], a.gpl != nullptr ? a.gpl[a.gid[v0 + tid]] : a.pick_less);
     changed = nl != s_old[tid];
     a.c_next[v0 + tid] = nl;
     if (changed && a.gdn != nullptr) atomicAdd(a.gdn + a.gid[v0 + tid], 1u);

@@ -128,6 +128,9 @@ struct SweepArgs {
   const int32_t* gid;
   const int32_t* gdone;
   uint32_t* gdn;
+  // Served form, null otherwise: graph g's own pick-less setting for this sweep
+  // (graphs that joined at different sweeps are at different iterations).
+  const int32_t* gpl;
   int32_t nchunks;
   int32_t nhubs;
   int32_t pick_less;
@@ -247,6 +250,17 @@ cudaError_t launch_batch_converge(const BatchGraph* gs, int count, const uint32_
                                   DevState* st, int l, int pick_less, double tol, cudaStream_t s);
 cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const int32_t* c,
                                  int64_t nv, cudaStream_t s);
+
+// Served form (lpa_batch.cu): per-graph stop test after a sweep, label carry-over into a
+// new packing (old_vb[g] < 0 for a new graph), output of the graphs that stopped.
+cudaError_t launch_serve_converge(const BatchGraph* gs, int count, const uint32_t* gdn,
+                                  int32_t* gdone, int32_t* giter, int32_t* gconv, int32_t* gpl,
+                                  int32_t* gfin, int max_iter, int rho, double tol,
+                                  cudaStream_t s);
+cudaError_t launch_carry_labels(const BatchGraph* gs, const int64_t* old_vb, const int32_t* gid,
+                                const int32_t* c_old, int32_t* c_new, int64_t nv, cudaStream_t s);
+cudaError_t launch_unpack_finished(const BatchGraph* gs, const int32_t* gid, const int32_t* gfin,
+                                   const int32_t* c, int64_t nv, cudaStream_t s);
 
 // Record the message returned by lpa_last_error() on this host thread; returns s.
 int set_last_error(int s, const char* msg);

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   }
   __shared__ int s_changed;
   if (tid == 0) {
-    const int nl = commit_label(choice, own, a.pick_less);
+    const int nl = commit_label(choice, own, a.gpl != nullptr ? a.gpl[a.gid[v]] : a.pick_less);
     a.c_next[v] = nl;
     s_changed = nl != own;
     if (nl != own) atomicAdd(a.dn + (blockIdx.x & (kDnSlots - 1)), 1ull);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
   }
   int changed = 0;
   if (v >= 0 && leaf == 0) {
-    const int nl = commit_label(choice, own, a.pick_less);
+    const int nl = commit_label(choice, own, a.gpl != nullptr ? a.gpl[g] : a.pick_less);
     a.c_next[v] = nl;
     changed = nl != own;
   }

@@ -129,6 +129,12 @@ _SIG = {
     "lpa_modularity_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
     "lpa_batch_detect": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
                                         ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
+    "lpa_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_int32, ctypes.c_size_t, _P, _P]),
+    "lpa_server_submit": (ctypes.c_int, [_P, _P, _P]),
+    "lpa_server_step": (ctypes.c_int, [_P, _P]),
+    "lpa_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P]),
+    "lpa_server_destroy": (ctypes.c_int, [_P]),
     "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "lpa_plan_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
@@ -385,6 +391,59 @@ def lpa_batch_detect(graphs, mode="mg", k=8, tol=0.05, max_iter=20,
     out = [{"iterations": int(stats[g].iterations), "converged": bool(stats[g].converged),
             "edges_scanned": int(stats[g].edges_scanned)} for g in range(count)]
     return out, changed[:count, :max_iter]
+
+
+class Server:
+    """Served form (``lpa_server_*``): submit device graphs, step, poll."""
+
+    def __init__(self, mode="mg", k=8, tol=0.05, max_iter=20, hbm_budget_bytes=0, **opts):
+        self.opt = make_options(**opts)
+        h = ctypes.c_void_p()
+        _check(load().lpa_server_create(_mode(mode), k, tol, max_iter, hbm_budget_bytes,
+                                        ctypes.byref(self.opt), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, offsets, indices, weights, labels_out) -> int:
+        g = lpa_graph(_ptr(offsets), _ptr(indices), _ptr(weights), int(offsets.numel() - 1),
+                      int(indices.numel()), _ptr(labels_out))
+        t = ctypes.c_uint64()
+        _check(load().lpa_server_submit(self.handle, ctypes.byref(g), ctypes.byref(t)))
+        self._keep[t.value] = (offsets, indices, weights, labels_out)
+        return int(t.value)
+
+    def step(self) -> int:
+        pending = ctypes.c_int32()
+        _check(load().lpa_server_step(self.handle, ctypes.byref(pending)))
+        return int(pending.value)
+
+    def poll(self, ticket: int):
+        """None while running, else the request's stat dict (the ticket is then forgotten)."""
+        done = ctypes.c_int32()
+        st = lpa_graph_stats()
+        _check(load().lpa_server_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(st)))
+        if not done.value:
+            return None
+        self._keep.pop(ticket, None)
+        return {"iterations": int(st.iterations), "converged": bool(st.converged),
+                "edges_scanned": int(st.edges_scanned)}
+
+    def close(self):
+        if self.handle:
+            load().lpa_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def detect(offsets, indices, weights=None, mode="mg", k=8, tol=0.05, max_iter=20,
