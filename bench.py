@@ -745,14 +745,13 @@ def run_serve(args):
         t_done = time.perf_counter() - start
         step_time += time.perf_counter() - t_step
         inflight_sum += len(inflight)
-        for tk in list(inflight):
+        for tk in srv.drain():
             st = srv.poll(tk)
-            if st is not None:
-                i, out = inflight.pop(tk)
-                done_at[i] = t_done
-                iters[i] = st["iterations"]
-                if i in check:
-                    outputs[i] = out
+            i, out = inflight.pop(tk)
+            done_at[i] = t_done
+            iters[i] = st["iterations"]
+            if i in check:
+                outputs[i] = out
     torch.cuda.synchronize(dev)
     clocks.mark("end")
     clk = clocks.stop()

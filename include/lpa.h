@@ -257,8 +257,11 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
  * bytes each) fits hbm_budget_bytes (0 = no limit; one request is always admitted when
  * none is resident), then runs one sweep of every resident graph -- each at its own
  * iteration, with its own pick-less setting and stop test (Alg. 1) -- and writes the
- * labels of the graphs that stopped.  A request's result equals lpa_detect_ex on its
- * graph alone, whatever else is resident.  One host thread drives a server; calls are
+ * labels of the graphs that stopped.  Resident graphs live in an arena: a new graph is
+ * appended (only its own CSR is copied), a stopped one leaves a slot the sweeps skip,
+ * and the live graphs are re-packed when dead slots hold more than half of the arena or
+ * a new graph does not fit.  A request's result equals lpa_detect_ex on its graph
+ * alone, whatever else is resident.  One host thread drives a server; calls are
  * ordered on opt->stream and each step synchronises it once.  LPA_PRUNE and labels_in
  * are not supported; LPA_VALIDATE checks each graph at submission. */
 typedef struct lpa_server_s* lpa_server;
@@ -275,6 +278,10 @@ lpa_status lpa_server_step(lpa_server server, int32_t* pending_out);
  * lpa_batch_detect.  A ticket reported done is forgotten (later polls: LPA_EINVAL). */
 lpa_status lpa_server_poll(lpa_server server, uint64_t ticket, int32_t* done,
                            lpa_graph_stats* stats);
+/* Tickets of the requests that finished since the last drain (at most cap of them, in
+ * finishing order; the rest stay for the next drain) into tickets (host), their number
+ * into count_out.  Lets a caller poll only the finished requests. */
+lpa_status lpa_server_drain(lpa_server server, uint64_t* tickets, int32_t cap, int32_t* count_out);
 /* Frees the server; requests not yet done are dropped (their outputs unspecified). */
 lpa_status lpa_server_destroy(lpa_server server);
 

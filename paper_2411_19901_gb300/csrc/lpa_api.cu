@@ -661,14 +661,21 @@ struct ServeReq {
   int64_t vb = -1;    // vertex base in the current packing while resident
 };
 
-// The resident graphs packed block-diagonally, their per-graph state and the plan over
-// the packed graph.  Rebuilt whenever the resident set changes; labels carry over.
+// The resident graphs packed block-diagonally in an arena with room to grow: graphs are
+// appended at the end of the used part (only their own CSR is copied, and the other
+// graphs' labels stay in place); a graph that stops stays as a dead slot that the sweeps
+// skip, until a compaction re-packs the live graphs into a fresh arena (labels carried
+// over, shifted to their new base).  The plan covers the used part and is rebuilt
+// whenever it changes.
 struct Packing {
   char* dev = nullptr;
-  int count = 0;
-  int64_t N = 0, M = 0;
+  int gcap = 0, count = 0;      // graph slots: capacity, used
+  int64_t ncap = 0, mcap = 0;   // vertex and entry capacity
+  int64_t N = 0, M = 0;         // used vertices and entries
+  int64_t dead_n = 0;           // vertices of dead slots
+  bool weighted = false;
   BatchGraph* tab = nullptr;
-  int64_t *vb = nullptr, *eb = nullptr, *off = nullptr, *old_vb = nullptr;
+  int64_t *bases = nullptr, *off = nullptr, *old_vb = nullptr;  // bases: scratch for appends
   int32_t* idx = nullptr;
   float* w = nullptr;
   int32_t* gid = nullptr;
@@ -697,12 +704,13 @@ struct lpa_server_s {
   size_t budget = 0, used = 0;
   uint64_t next = 1;
   std::deque<ServeReq*> waiting;
-  std::vector<ServeReq*> resident;
+  std::vector<ServeReq*> slots;  // per graph slot of the packing; nullptr = dead
+  int live = 0;
   std::unordered_map<uint64_t, ServeReq*> reqs;
+  std::vector<uint64_t> finished;  // tickets done since the last drain
   Packing pk;
-  bool dirty = false;
   int32_t* d_err = nullptr;      // validation scratch
-  int32_t* h_state = nullptr;    // page-locked: gfin, giter, gconv of the last step
+  int32_t* h_state = nullptr;    // page-locked: giter, gconv, gfin of the last step
   size_t h_state_cap = 0;
 };
 
@@ -714,115 +722,202 @@ void free_packing(Packing& P, cudaStream_t s) {
   P = Packing{};
 }
 
-lpa_status serve_repack(lpa_server_s* S) {
-  cudaStream_t s = S->stream;
-  const int count = (int)S->resident.size();
-  std::vector<int64_t> vb(count + 1, 0), eb(count + 1, 0), old_vb(count);
-  std::vector<BatchGraph> tab(count);
-  std::vector<int32_t> st(5 * (size_t)count, 0);  // gdone, giter, gconv, gpl, gfin
-  bool weighted = false;
-  const int rho = S->opt.pl_period;
-  for (int g = 0; g < count; ++g) {
-    ServeReq* r = S->resident[g];
-    tab[g] = BatchGraph{r->g.offsets, r->g.indices, r->g.weights, r->g.labels_out, vb[g], eb[g],
-                        r->g.m, r->g.n, 0};
-    old_vb[g] = r->vb;
-    vb[g + 1] = vb[g] + r->g.n;
-    eb[g + 1] = eb[g] + r->g.m;
-    weighted = weighted || (r->g.weights && r->g.m > 0);
-    st[(size_t)count + g] = r->iterations;
-    st[3 * (size_t)count + g] = (rho > 0 && r->iterations % rho == 0) ? 1 : 0;
-  }
-  const int64_t N = vb[count], M = eb[count];
-  if (N > 0x7ffffff0LL) return fail(LPA_EUNSUPPORTED, "resident vertices exceed int32 ids");
-  Packing P;
-  P.count = count;
-  P.N = N;
-  P.M = M;
+// A fresh arena with the given capacities (no graph yet).
+lpa_status alloc_packing(Packing& P, int gcap, int64_t ncap, int64_t mcap, bool weighted,
+                         cudaStream_t s) {
+  P = Packing{};
+  P.gcap = gcap;
+  P.ncap = ncap;
+  P.mcap = mcap;
+  P.weighted = weighted;
   size_t at = 0;
   auto take = [&](size_t bytes) {
     const size_t r = at;
     at = align256(at + bytes);
     return r;
   };
-  const size_t o_tab = take(sizeof(BatchGraph) * count), o_vb = take(8 * (size_t)(count + 1)),
-               o_eb = take(8 * (size_t)(count + 1)), o_ovb = take(8 * (size_t)count),
-               o_off = take(8 * (size_t)(N + 1)), o_idx = take(4 * (size_t)M + 4),
-               o_w = weighted ? take(4 * (size_t)M + 4) : 0, o_gid = take(4 * (size_t)N + 4),
-               o_st = take(4 * 5 * (size_t)count), o_gdn = take(4 * (size_t)count),
-               o_l0 = take(4 * (size_t)N + 4), o_l1 = take(4 * (size_t)N + 4);
+  const size_t o_tab = take(sizeof(BatchGraph) * gcap), o_b = take(8 * 2 * (size_t)(gcap + 1)),
+               o_ovb = take(8 * (size_t)gcap), o_off = take(8 * (size_t)(ncap + 1)),
+               o_idx = take(4 * (size_t)mcap + 16), o_w = weighted ? take(4 * (size_t)mcap + 16) : 0,
+               o_gid = take(4 * (size_t)ncap + 4), o_st = take(4 * 5 * (size_t)gcap),
+               o_gdn = take(4 * (size_t)gcap), o_l0 = take(4 * (size_t)ncap + 4),
+               o_l1 = take(4 * (size_t)ncap + 4);
   LPA_CUDA(cudaMallocAsync((void**)&P.dev, at, s));
   P.tab = (BatchGraph*)(P.dev + o_tab);
-  P.vb = (int64_t*)(P.dev + o_vb);
-  P.eb = (int64_t*)(P.dev + o_eb);
+  P.bases = (int64_t*)(P.dev + o_b);
   P.old_vb = (int64_t*)(P.dev + o_ovb);
   P.off = (int64_t*)(P.dev + o_off);
   P.idx = (int32_t*)(P.dev + o_idx);
   P.w = weighted ? (float*)(P.dev + o_w) : nullptr;
   P.gid = (int32_t*)(P.dev + o_gid);
-  int32_t* d_st = (int32_t*)(P.dev + o_st);
-  P.gdone = d_st;
-  P.giter = d_st + count;
-  P.gconv = d_st + 2 * count;
-  P.gpl = d_st + 3 * count;
-  P.gfin = d_st + 4 * count;
+  int32_t* st = (int32_t*)(P.dev + o_st);
+  P.gdone = st;
+  P.giter = st + gcap;
+  P.gconv = st + 2 * (size_t)gcap;
+  P.gpl = st + 3 * (size_t)gcap;
+  P.gfin = st + 4 * (size_t)gcap;
   P.gdn = (uint32_t*)(P.dev + o_gdn);
   P.lab[0] = (int32_t*)(P.dev + o_l0);
   P.lab[1] = (int32_t*)(P.dev + o_l1);
-  cudaError_t ce = cudaMemcpyAsync(P.tab, tab.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.vb, vb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.eb, eb.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.old_vb, old_vb.data(), 8 * (size_t)count, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_st, st.data(), 4 * 5 * (size_t)count, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(P.off + N, &M, sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess)
-    ce = launch_pack_batch(P.tab, P.vb, P.eb, count, N, M, P.off, P.idx, P.w, P.gid, false, nullptr, s);
-  if (ce == cudaSuccess)
-    ce = launch_carry_labels(P.tab, P.old_vb, P.gid, S->pk.lab[S->pk.cur], P.lab[0], N, s);
-  // host vectors must outlive the pageable copies: wait for them before returning
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  if (ce != cudaSuccess) {
-    cudaFreeAsync(P.dev, s);
-    return fail(LPA_ECUDA, "server repack: %s", cudaGetErrorString(ce));
+  return LPA_OK;
+}
+
+// Append graphs rs at the end of P's used part (capacity checked by the caller).  Each
+// graph's iteration count comes from its request; old_vb[g] >= 0 carries its labels
+// from `from` (a compaction), else it starts from C[v] = v.
+lpa_status append_graphs(Packing& P, const std::vector<ServeReq*>& rs, const int32_t* from,
+                         int rho, cudaStream_t s) {
+  const int c = (int)rs.size();
+  if (c == 0) return LPA_OK;
+  std::vector<BatchGraph> tab(c);
+  std::vector<int64_t> bases(2 * (size_t)(c + 1), 0), old_vb(c);
+  std::vector<int32_t> st(5 * (size_t)c, 0);
+  int64_t nv = 0, ne = 0;
+  bool carry = false;
+  for (int g = 0; g < c; ++g) {
+    ServeReq* r = rs[g];
+    tab[g] = BatchGraph{r->g.offsets, r->g.indices, r->g.weights, r->g.labels_out, P.N + nv,
+                        P.M + ne, r->g.m, r->g.n, 0};
+    old_vb[g] = r->vb;
+    carry = carry || r->vb >= 0;
+    nv += r->g.n;
+    ne += r->g.m;
+    bases[g + 1] = nv;
+    bases[(size_t)(c + 1) + g + 1] = ne;
+    st[(size_t)c + g] = r->iterations;
+    st[3 * (size_t)c + g] = (rho > 0 && r->iterations % rho == 0) ? 1 : 0;
   }
+  const int g0 = P.count;
+  const int64_t endM = P.M + ne;
+  cudaError_t ce = cudaMemcpyAsync(P.tab + g0, tab.data(), sizeof(BatchGraph) * c,
+                                   cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(P.bases, bases.data(), 8 * bases.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(P.old_vb + g0, old_vb.data(), 8 * (size_t)c, cudaMemcpyHostToDevice, s);
+  for (int q = 0; q < 5 && ce == cudaSuccess; ++q)  // gdone, giter, gconv, gpl, gfin
+    ce = cudaMemcpyAsync(P.gdone + (size_t)q * P.gcap + g0, st.data() + (size_t)q * c,
+                         4 * (size_t)c, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(P.off + P.N + nv, &endM, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = launch_pack_batch(P.tab + g0, P.bases, P.bases + (c + 1), c, nv, ne, P.off + P.N,
+                           P.idx + P.M, P.w ? P.w + P.M : nullptr, P.gid + P.N, g0, false,
+                           nullptr, s);
+  if (ce == cudaSuccess) {
+    if (carry)
+      ce = launch_carry_labels(P.tab, P.old_vb, P.gid + P.N, from, P.lab[P.cur] + P.N, P.N, nv, s);
+    else
+      ce = launch_iota_i32(P.lab[P.cur] + P.N, P.N, nv, s);
+  }
+  // the host vectors must outlive the copies from pageable memory
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(LPA_ECUDA, "server append: %s", cudaGetErrorString(ce));
+  for (int g = 0; g < c; ++g) rs[g]->vb = P.N + bases[g];
+  P.count += c;
+  P.N += nv;
+  P.M = endM;
+  return LPA_OK;
+}
+
+// The plan over the packing's used part (rebuilt after every change of it).
+lpa_status replan(lpa_server_s* S) {
+  Packing& P = S->pk;
+  if (P.plan) {
+    destroy_plan(P.plan);
+    P.plan = nullptr;
+  }
+  if (P.N == 0) return LPA_OK;
   lpa_options po = S->opt;
   po.flags &= ~(LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY | LPA_PRUNE);
   po.workspace = nullptr;
   po.workspace_bytes = 0;
   po.labels_in = nullptr;
-  lpa_status rs = plan_create(P.off, P.idx, P.w, (int32_t)N, M, (lpa_mode)S->mode, S->k, &po, &P.plan);
-  if (rs != LPA_OK) {
-    cudaFreeAsync(P.dev, s);
-    return rs;
+  return plan_create(P.off, P.idx, P.w, (int32_t)P.N, P.M, (lpa_mode)S->mode, S->k, &po, &P.plan);
+}
+
+// Admit fresh requests: append them if they fit the arena, else (or when dead slots hold
+// more than half of it) compact the live graphs and the fresh ones into a new arena.
+lpa_status serve_admit(lpa_server_s* S, std::vector<ServeReq*>& fresh, bool compact) {
+  cudaStream_t s = S->stream;
+  Packing& P = S->pk;
+  int64_t nv = 0, ne = 0;
+  bool w = false;
+  for (ServeReq* r : fresh) {
+    nv += r->g.n;
+    ne += r->g.m;
+    w = w || (r->g.weights && r->g.m > 0);
   }
-  free_packing(S->pk, s);
-  S->pk = P;
-  for (int g = 0; g < count; ++g) S->resident[g]->vb = vb[g];
-  return LPA_OK;
+  const bool fits = P.dev && P.count + (int)fresh.size() <= P.gcap && P.N + nv <= P.ncap &&
+                    P.M + ne <= P.mcap && (!w || P.weighted) && !compact;
+  if (fits) {
+    lpa_status rs = append_graphs(P, fresh, nullptr, S->opt.pl_period, s);
+    if (rs != LPA_OK) return rs;
+    for (ServeReq* r : fresh) S->slots.push_back(r);
+  } else {
+    std::vector<ServeReq*> live;
+    int64_t lv = 0, le = 0;
+    bool lw = w;
+    for (ServeReq* r : S->slots)
+      if (r) {
+        live.push_back(r);
+        lv += r->g.n;
+        le += r->g.m;
+        lw = lw || (r->g.weights && r->g.m > 0);
+      }
+    const int gc = (int)(live.size() + fresh.size());
+    if (lv + nv > 0x7ffffff0LL) return fail(LPA_EUNSUPPORTED, "resident vertices exceed int32 ids");
+    Packing Q;
+    lpa_status rs = alloc_packing(Q, std::max(64, 2 * gc), std::max<int64_t>(1 << 16, 2 * (lv + nv)),
+                                  std::max<int64_t>(1 << 20, 2 * (le + ne)), lw, s);
+    if (rs != LPA_OK) return rs;
+    if (!live.empty()) {
+      rs = append_graphs(Q, live, P.lab[P.cur], S->opt.pl_period, s);
+      if (rs != LPA_OK) {
+        free_packing(Q, s);
+        return rs;
+      }
+    }
+    for (ServeReq* r : fresh) r->vb = -1;
+    rs = append_graphs(Q, fresh, nullptr, S->opt.pl_period, s);
+    if (rs != LPA_OK) {
+      free_packing(Q, s);
+      return rs;
+    }
+    free_packing(P, s);
+    S->pk = Q;
+    S->slots = live;
+    for (ServeReq* r : fresh) S->slots.push_back(r);
+  }
+  return replan(S);
 }
 
 lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
   cudaStream_t s = S->stream;
+  std::vector<ServeReq*> fresh;
+  size_t used = S->used;
   while (!S->waiting.empty()) {  // admission by HBM footprint, first come first served
     ServeReq* r = S->waiting.front();
-    if (S->budget && S->used + r->foot > S->budget && !S->resident.empty()) break;
+    if (S->budget && used + r->foot > S->budget && (S->live > 0 || !fresh.empty())) break;
     S->waiting.pop_front();
     r->state = 1;
     r->vb = -1;
-    S->resident.push_back(r);
-    S->used += r->foot;
-    S->dirty = true;
+    fresh.push_back(r);
+    used += r->foot;
   }
-  if (S->resident.empty()) {
+  Packing& P0 = S->pk;
+  const bool compact = P0.N > 0 && 2 * P0.dead_n > P0.N;
+  if (!fresh.empty() || compact) {
+    lpa_status rs = serve_admit(S, fresh, compact);
+    if (rs != LPA_OK) return rs;
+    S->used = used;
+    S->live += (int)fresh.size();
+  }
+  Packing& P = S->pk;
+  if (S->live == 0 || !P.plan) {
     if (pending_out) *pending_out = (int32_t)S->waiting.size();
     return LPA_OK;
   }
-  if (S->dirty) {
-    lpa_status rs = serve_repack(S);
-    if (rs != LPA_OK) return rs;
-    S->dirty = false;
-  }
-  Packing& P = S->pk;
   LPA_CUDA(launch_fill_i32((int32_t*)P.gdn, 0, P.count, s));
   LPA_CUDA(launch_fill_i32(P.gfin, 0, P.count, s));
   SweepArgs a = sweep_args(P.plan, P.lab[P.cur], P.lab[1 - P.cur], 0, P.plan->dn, nullptr);
@@ -835,38 +930,42 @@ lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
                                  S->max_iter, S->opt.pl_period, S->tol, s));
   P.cur ^= 1;
   LPA_CUDA(launch_unpack_finished(P.tab, P.gid, P.gfin, P.lab[P.cur], P.N, s));
-  if (S->h_state_cap < 3 * (size_t)P.count) {
+  if (S->h_state_cap < 3 * (size_t)P.gcap) {
     if (S->h_state) cudaFreeHost(S->h_state);
     S->h_state = nullptr;
     S->h_state_cap = 0;
-    LPA_CUDA(cudaMallocHost((void**)&S->h_state, 4 * 3 * (size_t)P.count));
-    S->h_state_cap = 3 * (size_t)P.count;
+    LPA_CUDA(cudaMallocHost((void**)&S->h_state, 4 * 3 * (size_t)P.gcap));
+    S->h_state_cap = 3 * (size_t)P.gcap;
   }
-  // giter, gconv are adjacent in the state block; gfin follows gpl
-  LPA_CUDA(cudaMemcpyAsync(S->h_state, P.giter, 4 * 2 * (size_t)P.count, cudaMemcpyDeviceToHost, s));
-  LPA_CUDA(cudaMemcpyAsync(S->h_state + 2 * P.count, P.gfin, 4 * (size_t)P.count,
+  LPA_CUDA(cudaMemcpyAsync(S->h_state, P.giter, 4 * (size_t)P.count, cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(S->h_state + P.count, P.gconv, 4 * (size_t)P.count,
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(S->h_state + 2 * (size_t)P.count, P.gfin, 4 * (size_t)P.count,
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
-  std::vector<ServeReq*> keep;
-  keep.reserve(S->resident.size());
   for (int g = 0; g < P.count; ++g) {
-    ServeReq* r = S->resident[g];
+    ServeReq* r = S->slots[g];
+    if (!r) continue;
     r->iterations = S->h_state[g];
-    if (S->h_state[2 * P.count + g]) {
+    if (S->h_state[2 * (size_t)P.count + g]) {
       r->state = 2;
       r->converged = S->h_state[P.count + g];
       r->vb = -1;
       S->used -= r->foot;
-      S->dirty = true;
-    } else {
-      keep.push_back(r);
+      S->slots[g] = nullptr;
+      S->live -= 1;
+      P.dead_n += r->g.n;
+      S->finished.push_back(r->ticket);
     }
   }
-  if (S->dirty) {
-    // the next packing carries labels by each graph's base in this one
-    S->resident.swap(keep);
+  if (S->live == 0) {  // everything stopped: the arena is empty again
+    if (P.plan) destroy_plan(P.plan);
+    P.plan = nullptr;
+    P.count = 0;
+    P.N = P.M = P.dead_n = 0;
+    S->slots.clear();
   }
-  if (pending_out) *pending_out = (int32_t)(S->resident.size() + S->waiting.size());
+  if (pending_out) *pending_out = (int32_t)(S->live + S->waiting.size());
   return LPA_OK;
 }
 
@@ -1159,7 +1258,7 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
   const bool validate = (o.flags & LPA_VALIDATE) != 0;
   if (ce == cudaSuccess)
     ce = launch_pack_batch(d_tab, (const int64_t*)(dev + o_vb), (const int64_t*)(dev + o_eb),
-                           count, N, M, d_off, d_idx, d_w, d_gid, validate, d_err, s);
+                           count, N, M, d_off, d_idx, d_w, d_gid, 0, validate, d_err, s);
   if (ce != cudaSuccess)
     return cleanup(fail(LPA_ECUDA, "batch packing: %s", cudaGetErrorString(ce)));
   if (validate) {
@@ -1306,6 +1405,15 @@ lpa_status lpa_server_poll(lpa_server S, uint64_t ticket, int32_t* done, lpa_gra
     S->reqs.erase(it);
     delete r;
   }
+  return LPA_OK;
+}
+
+lpa_status lpa_server_drain(lpa_server S, uint64_t* tickets, int32_t cap, int32_t* count) {
+  if (!S || !count || (cap > 0 && !tickets)) return fail(LPA_EINVAL, "NULL argument");
+  const int32_t c = (int32_t)std::min<size_t>((size_t)std::max(cap, 0), S->finished.size());
+  for (int32_t i = 0; i < c; ++i) tickets[i] = S->finished[i];
+  S->finished.erase(S->finished.begin(), S->finished.begin() + c);
+  *count = c;
   return LPA_OK;
 }
 

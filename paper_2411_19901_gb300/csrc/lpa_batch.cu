@@ -24,8 +24,8 @@ __device__ __forceinline__ int find_graph(const int64_t* __restrict__ base, int 
 // Offsets and graph ids of the packed vertices; with validate, checks each graph's
 // offsets (first 0, non-decreasing, last = m_g).
 __global__ void pack_offsets_kernel(const BatchGraph* __restrict__ gs, const int64_t* __restrict__ vb,
-                                    int count, int64_t nv, int64_t* off, int32_t* gid, int validate,
-                                    int32_t* err) {
+                                    int count, int64_t nv, int64_t* off, int32_t* gid, int g0,
+                                    int validate, int32_t* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
     // graphs with n_g = 0 share a base with the next one; find_graph takes the last
@@ -34,7 +34,7 @@ __global__ void pack_offsets_kernel(const BatchGraph* __restrict__ gs, const int
     const int64_t i = v - vb[g];
     const int64_t o0 = G.off[i], o1 = G.off[i + 1];
     off[v] = o0 + G.eb;
-    gid[v] = g;
+    gid[v] = g0 + g;
     if (validate && ((i == 0 && o0 != 0) || o1 < o0 || (i + 1 == G.n && o1 != G.m)))
       atomicOr(err, kErrOffsets);
   }
@@ -148,16 +148,18 @@ __global__ void serve_converge_kernel(const BatchGraph* __restrict__ gs, int cou
   gpl[g] = (rho > 0 && (l + 1) % rho == 0) ? 1 : 0;
 }
 
-// New packing of the resident graphs: a graph that was resident before (old_vb[g] >= 0)
-// carries its labels over, shifted to its new base; a new graph starts from C[i] = i.
+// Re-packed graphs: vertices [v0, v0 + nv) of the new packing (gid and c_new point at
+// v0); a graph that was resident before (old_vb[g] >= 0) carries its labels over,
+// shifted to its new base; a new graph starts from C[v] = v.
 __global__ void carry_labels_kernel(const BatchGraph* __restrict__ gs,
                                     const int64_t* __restrict__ old_vb, const int32_t* __restrict__ gid,
-                                    const int32_t* __restrict__ c_old, int32_t* c_new, int64_t nv) {
+                                    const int32_t* __restrict__ c_old, int32_t* c_new, int64_t v0,
+                                    int64_t nv) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
-    const int g = gid[v];
-    const int64_t ob = old_vb[g], nb = gs[g].vb;
-    c_new[v] = ob < 0 ? (int32_t)v : (int32_t)(c_old[ob + (v - nb)] - ob + nb);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const int g = gid[i];
+    const int64_t v = v0 + i, ob = old_vb[g], nb = gs[g].vb;
+    c_new[i] = ob < 0 ? (int32_t)v : (int32_t)(c_old[ob + (v - nb)] - ob + nb);
   }
 }
 
@@ -174,6 +176,13 @@ __global__ void unpack_finished_kernel(const BatchGraph* __restrict__ gs, const 
   }
 }
 
+// p[i] = start + i: the initial labels C[v] = v of vertices appended at base start.
+__global__ void iota_i32_kernel(int32_t* p, int64_t start, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    p[i] = (int32_t)(start + i);
+}
+
 inline unsigned grid_of(int64_t n) {
   const int64_t g = (n + 255) / 256;
   return (unsigned)(g < 152 * 32 ? (g > 0 ? g : 1) : 152 * 32);
@@ -183,9 +192,9 @@ inline unsigned grid_of(int64_t n) {
 
 cudaError_t launch_pack_batch(const BatchGraph* gs, const int64_t* vb, const int64_t* eb, int count,
                               int64_t nv, int64_t ne, int64_t* off, int32_t* idx, float* w,
-                              int32_t* gid, bool validate, int32_t* err, cudaStream_t s) {
+                              int32_t* gid, int g0, bool validate, int32_t* err, cudaStream_t s) {
   if (nv > 0) {
-    pack_offsets_kernel<<<grid_of(nv), 256, 0, s>>>(gs, vb, count, nv, off, gid, validate, err);
+    pack_offsets_kernel<<<grid_of(nv), 256, 0, s>>>(gs, vb, count, nv, off, gid, g0, validate, err);
     count_launch();
   }
   if (ne > 0) {
@@ -219,6 +228,13 @@ cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_iota_i32(int32_t* p, int64_t start, int64_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  iota_i32_kernel<<<grid_of(count), 256, 0, s>>>(p, start, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_serve_converge(const BatchGraph* gs, int count, const uint32_t* gdn,
                                   int32_t* gdone, int32_t* giter, int32_t* gconv, int32_t* gpl,
                                   int32_t* gfin, int max_iter, int rho, double tol,
@@ -231,9 +247,10 @@ cudaError_t launch_serve_converge(const BatchGraph* gs, int count, const uint32_
 }
 
 cudaError_t launch_carry_labels(const BatchGraph* gs, const int64_t* old_vb, const int32_t* gid,
-                                const int32_t* c_old, int32_t* c_new, int64_t nv, cudaStream_t s) {
+                                const int32_t* c_old, int32_t* c_new, int64_t v0, int64_t nv,
+                                cudaStream_t s) {
   if (nv == 0) return cudaSuccess;
-  carry_labels_kernel<<<grid_of(nv), 256, 0, s>>>(gs, old_vb, gid, c_old, c_new, nv);
+  carry_labels_kernel<<<grid_of(nv), 256, 0, s>>>(gs, old_vb, gid, c_old, c_new, v0, nv);
   count_launch();
   return cudaGetLastError();
 }

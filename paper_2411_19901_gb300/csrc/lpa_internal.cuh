@@ -240,9 +240,13 @@ int modularity_partials(int32_t n);
 inline int64_t num_segments(int64_t n) { return (n + kSegment - 1) / kSegment; }
 
 // Batched form (lpa_batch.cu).  vb / eb: count + 1 ascending vertex / entry bases.
+// gs[0, count) are written from packed vertex / entry 0 of off / idx / w / gid (callers
+// appending to a packing pass pointers past its used part); gid = g0 + g; vb / eb are
+// count + 1 bases relative to those pointers, while gs[g].vb / eb are absolute.
 cudaError_t launch_pack_batch(const BatchGraph* gs, const int64_t* vb, const int64_t* eb, int count,
                               int64_t nv, int64_t ne, int64_t* off, int32_t* idx, float* w,
-                              int32_t* gid, bool validate, int32_t* err, cudaStream_t s);
+                              int32_t* gid, int g0, bool validate, int32_t* err, cudaStream_t s);
+cudaError_t launch_iota_i32(int32_t* p, int64_t start, int64_t count, cudaStream_t s);
 cudaError_t launch_batch_init(const BatchGraph* gs, int count, int32_t* gdone, int32_t* giter,
                               int32_t* gconv, int32_t* active, DevState* st, cudaStream_t s);
 cudaError_t launch_batch_converge(const BatchGraph* gs, int count, const uint32_t* gdn_l,
@@ -252,13 +256,15 @@ cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const
                                  int64_t nv, cudaStream_t s);
 
 // Served form (lpa_batch.cu): per-graph stop test after a sweep, label carry-over into a
-// new packing (old_vb[g] < 0 for a new graph), output of the graphs that stopped.
+// new packing (old_vb[g] < 0 for a new graph; gid and c_new point at vertex v0), output
+// of the graphs that stopped.
 cudaError_t launch_serve_converge(const BatchGraph* gs, int count, const uint32_t* gdn,
                                   int32_t* gdone, int32_t* giter, int32_t* gconv, int32_t* gpl,
                                   int32_t* gfin, int max_iter, int rho, double tol,
                                   cudaStream_t s);
 cudaError_t launch_carry_labels(const BatchGraph* gs, const int64_t* old_vb, const int32_t* gid,
-                                const int32_t* c_old, int32_t* c_new, int64_t nv, cudaStream_t s);
+                                const int32_t* c_old, int32_t* c_new, int64_t v0, int64_t nv,
+                                cudaStream_t s);
 cudaError_t launch_unpack_finished(const BatchGraph* gs, const int32_t* gid, const int32_t* gfin,
                                    const int32_t* c, int64_t nv, cudaStream_t s);
 

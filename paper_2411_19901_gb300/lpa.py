@@ -134,6 +134,7 @@ _SIG = {
     "lpa_server_submit": (ctypes.c_int, [_P, _P, _P]),
     "lpa_server_step": (ctypes.c_int, [_P, _P]),
     "lpa_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P]),
+    "lpa_server_drain": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "lpa_server_destroy": (ctypes.c_int, [_P]),
     "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
@@ -416,6 +417,14 @@ class Server:
         pending = ctypes.c_int32()
         _check(load().lpa_server_step(self.handle, ctypes.byref(pending)))
         return int(pending.value)
+
+    def drain(self, cap: int = 4096) -> list:
+        """Tickets finished since the last drain."""
+        buf = (ctypes.c_uint64 * max(cap, 1))()
+        cnt = ctypes.c_int32()
+        _check(load().lpa_server_drain(self.handle, ctypes.cast(buf, ctypes.c_void_p), cap,
+                                       ctypes.byref(cnt)))
+        return [int(buf[i]) for i in range(cnt.value)]
 
     def poll(self, ticket: int):
         """None while running, else the request's stat dict (the ticket is then forgotten)."""

@@ -112,3 +112,28 @@ def test_server_edge_cases(lpa):
         assert np.array_equal(tt[3].cpu().numpy(), np.arange(g.n))
     with pytest.raises(lpa.LpaError, match="LPA_PRUNE"):
         lpa.Server(mode="mg", prune=True)
+
+
+def test_arena_appends_compacts_and_drains(lpa):
+    """Thirty requests over thirty steps: the arena appends, leaves dead slots, compacts;
+    drain lists exactly the finished tickets and every result matches the oracle."""
+    gs = [synth.sbm_member(g, seed=4, nmin=100, nmax=2500) for g in range(30)]
+    refs = [oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG, threads=4) for g in gs]
+    outs = {}
+    with lpa.Server(mode="mg") as srv:
+        inflight = {}
+        for step in range(400):
+            if step < 30:
+                t = tensors(gs[step])
+                inflight[srv.submit(*t)] = (step, t)
+            srv.step()
+            for tk in srv.drain():
+                i, t = inflight.pop(tk)
+                st = srv.poll(tk)
+                assert st is not None and st["iterations"] == refs[i]["iterations"]
+                outs[i] = t[3].cpu().numpy()
+            if step >= 30 and not inflight:
+                break
+        assert not inflight and srv.drain() == []
+    for i in range(30):
+        assert np.array_equal(outs[i], refs[i]["labels"]), i
