@@ -493,7 +493,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "one sweep: sweep_hub_kernel and sweep_lane_kernel "
-                               "<MGSketch<8>, weighted, runs> (concurrent, fork/join)",
+                               "<MGSketch<8>, weighted> (concurrent, fork/join)",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs",
                      # the second fraction: measured DRAM bytes of one sweep over its time

@@ -163,7 +163,6 @@ struct lpa_plan_s {
   float* tab_vals = nullptr;
   int64_t nchunks = 0, nhubs = 0, hub_edges = 0;
   double setup_ms = 0.0;
-  bool exact_sums = false;  // every sum of a row's weights is exact in fp32
   std::vector<cudaEvent_t> events;  // timing pairs, created on demand
   DevState* host_state = nullptr;   // page-locked mirrors
   unsigned long long* host_dn = nullptr;
@@ -222,8 +221,7 @@ cudaError_t launch_sketch_sweep(const lpa_plan_s* p, const SweepArgs& a, cudaStr
   if (p->mode == kMG && (literal || rescan))
     return launch_sweep_mg_variant(p->k, literal, rescan, p->w != nullptr, a, p->wp, p->stream,
                                    s_hub);
-  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, p->exact_sums, a, p->wp, p->stream,
-                           s_hub);
+  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, a, p->wp, p->stream, s_hub);
 }
 
 cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
@@ -282,7 +280,8 @@ lpa_status bin_classes(lpa_plan_s* p) {
   LPA_CUDA(launch_scan_counts(lcnt, nwin, lane_prefix, s));
   LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, (int4*)wp.hub_desc,
                                ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
-  LPA_CUDA(launch_weight_profile(p->off, p->w, n, p->m, counts, s));
+  // the longest row (the weights are not read: only row lengths matter here)
+  LPA_CUDA(launch_weight_profile(p->off, nullptr, n, p->m, counts, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 3,
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls + 3, hub_prefix + nwin, sizeof(int64_t),
@@ -292,13 +291,6 @@ lpa_status bin_classes(lpa_plan_s* p) {
   LPA_CUDA(cudaStreamSynchronize(s));
   const double dmax = (double)p->host_cls[2];
   if (dmax > 2147483647.0) return fail(LPA_EUNSUPPORTED, "a row has more than 2^31 - 1 entries");
-  {
-    const bool integral = p->host_cls[0] != 0;
-    unsigned bits = (unsigned)p->host_cls[1];
-    float wmax;
-    memcpy(&wmax, &bits, sizeof(wmax));
-    p->exact_sums = integral && (double)wmax * dmax <= 16777216.0;
-  }
   const int64_t nhubs = (int64_t)p->host_cls[3], nlanes = (int64_t)p->host_cls[4];
   if (nhubs < 0 || nhubs > ly.hub_cap || nlanes < 0 || nlanes > ly.lane_cap)
     return fail(LPA_EINTERNAL, "window binning counted %lld hubs and %lld lanes", (long long)nhubs,

@@ -20,7 +20,6 @@ struct MGSketch {
   float val[K];
   unsigned em;
   static constexpr int kSlots = K;
-  static constexpr bool kRunMergeable = true;
 
   __device__ __forceinline__ void init(int /*own*/) {
 #pragma unroll
@@ -135,14 +134,12 @@ struct MGSketch {
 // ablation): a slot whose key equals c takes += w whatever its value; otherwise the
 // lowest slot of value exactly 0 takes (c, w); otherwise every slot loses w and c is
 // dropped.  Values may go negative; merges feed every slot of non-zero value; the
-// choice is the largest positive value.  Consecutive equal labels are not foldable
-// (a full sketch drops the first and may then have room for the second).
+// choice is the largest positive value.
 template <int K>
 struct MGLiteral {
   int key[K];
   float val[K];
   static constexpr int kSlots = K;
-  static constexpr bool kRunMergeable = false;
 
   __device__ __forceinline__ void init(int /*own*/) {
 #pragma unroll
@@ -262,7 +259,6 @@ struct BMState {
   int c;
   float w;
   static constexpr int kSlots = 1;
-  static constexpr bool kRunMergeable = false;
 
   __device__ __forceinline__ void init(int own) {
     c = own;
@@ -352,48 +348,13 @@ __device__ __forceinline__ int4 gather_group(const int32_t* __restrict__ lab, co
   return make_int4(c[0], c[1], c[2], c[3]);
 }
 
-// Feeds kept (label, weight) pairs into a state.  With RUNS, consecutive pairs of one
-// label are added as one pair of summed weight: for the Misra-Gries sketch with exact
-// arithmetic, add(c, a) then add(c, b) leaves the same slots as add(c, a + b) (a hit
-// adds both; an insert or a decrement followed by a hit or a re-insert ends with the
-// same remainder in the same slot), so the result is unchanged when every sum of the
-// row's weights is an exactly representable fp32 value.
-template <class S, bool RUNS>
-struct Feeder {
-  S& st;
-  int rc;
-  float rw;
-  __device__ __forceinline__ explicit Feeder(S& s) : st(s), rc(-1), rw(0.f) {}
-  __device__ __forceinline__ void push(int c, float w) {
-    if (c < 0) return;
-    if (!RUNS) {
-      st.add(c, w);
-      return;
-    }
-    if (c == rc) {
-      rw += w;
-    } else {
-      if (rc >= 0) st.add(rc, rw);
-      rc = c;
-      rw = w;
-    }
-  }
-  __device__ __forceinline__ void flush() {
-    if (RUNS && rc >= 0) st.add(rc, rw);
-  }
-  __device__ __forceinline__ void reset() {
-    rc = -1;
-    rw = 0.f;
-  }
-};
-
 // Fold positions [b, e) of the CSR, in order, into st: st.add(C[j], w) for every kept
 // position.  The range is read as aligned groups of four (16-byte index and weight
 // loads); only the first and last group carry a mask.  Software pipeline with three
 // register sets rotated by unrolling (no moves of registers with loads in flight): while
 // group k is folded, the labels of group k+1 are being gathered and group k+2 is being
 // loaded.
-template <class S, bool WT, bool SKIP_SELF, bool RUNS = false>
+template <class S, bool WT, bool SKIP_SELF>
 __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ idx,
                                            const float* __restrict__ wts,
                                            const int32_t* __restrict__ lab, int64_t m,
@@ -406,7 +367,6 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
   const bool tail_unsafe = g0 + 4 * (int64_t)ng > m;  // last group crosses the array end
   const int4* __restrict__ ip = reinterpret_cast<const int4*>(idx + g0);
   const float4* __restrict__ wp = reinterpret_cast<const float4*>(wts + g0);
-  Feeder<S, RUNS> fd(st);
 
   auto load = [&](int k, int4& X, float4& W) {
     if (tail_unsafe && k == ng - 1) {
@@ -428,7 +388,7 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
   auto fold = [&](int4 C, float4 W) {
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
-      fd.push(C.x, W.x);
+      if (C.x >= 0) st.add(C.x, W.x);
       C = make_int4(C.y, C.z, C.w, -1);
       W = make_float4(W.y, W.z, W.w, 0.f);
     }
@@ -450,7 +410,6 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
     LPA_STEP(X2, W2, X0, W0, X1, W1)
   }
 #undef LPA_STEP
-  fd.flush();
 }
 
 // ------------------------------------------------------------ work decomposition

@@ -170,14 +170,13 @@ struct BinArgs {
 };
 
 // Host-side launchers (stream-ordered, no synchronisation).
-// Sketch modes (MG, BM): warp-per-row kernel over a WarpPlan.
-// runs: fold runs of equal labels as one add (MG; only when row sums are exact in fp32).
+// Sketch modes (MG, BM): hub and lane kernels over a WarpPlan.
 // The hub kernel goes to s_hub, the lane kernel to s.
-cudaError_t launch_sweep_warp(int mode, int k, bool weighted, bool runs, const SweepArgs& a,
+cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
                               const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
-cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+cudaError_t launch_sweep_mg16(bool weighted, const SweepArgs& a, const WarpPlan& p,
                               cudaStream_t s, cudaStream_t s_hub);
-cudaError_t launch_sweep_mg32(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+cudaError_t launch_sweep_mg32(bool weighted, const SweepArgs& a, const WarpPlan& p,
                               cudaStream_t s, cudaStream_t s_hub);
 // MG ablations (at least one of literal, rescan set): paper-literal accumulate and / or
 // double scan, hub kernel on s_hub and lane kernel on s as launch_sweep_warp.

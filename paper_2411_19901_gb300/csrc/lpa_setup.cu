@@ -177,13 +177,18 @@ __global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t
 
 // ------------------------------------------------- binning for the warp sweep
 
-// Sort key of a vertex with d positions inside its window: 0 hub; 1 + c for mid class c
-// (larger L and longer leaves first); 1 + kMidClasses + (kLowKeys - 1 - min(d, kLowKeys-1))
-// for a one-leaf row (longer rows first).
-__device__ __forceinline__ int window_key(int64_t d, int e0, int lmax) {
+// Sort key of a vertex with d positions starting at CSR position b inside its window: 0
+// hub; 1 + c for mid class c (larger L and longer leaves first); for a one-leaf row
+// 1 + kMidClasses + (kLowKeys - 1 - min(a, kLowKeys - 1)) with a = d + (b mod 4), the
+// row's span in 16-byte groups' positions, so the rows of a warp read the same number of
+// aligned groups (longer spans first).
+__device__ __forceinline__ int window_key(int64_t d, int64_t b, int e0, int lmax) {
   const int L = leaf_count(d, e0, lmax);
   if (d > kHubDegree || L > kMaxWarpLeaves) return 0;
-  if (L == 1) return 1 + kMidClasses + (kLowKeys - 1 - (int)(d < kLowKeys ? d : kLowKeys - 1));
+  if (L == 1) {
+    const int64_t a = d + (b & 3);
+    return 1 + kMidClasses + (kLowKeys - 1 - (int)(a < kLowKeys ? a : kLowKeys - 1));
+  }
   const int lidx = 5 - (31 - __clz(L));  // L = 32 -> 0 ... L = 2 -> 4
   int sub = (int)(((d / L) * 4) / e0) - 4;  // leaf length quarter in [e0, 2 e0)
   sub = sub < 0 ? 0 : (sub > kMidSub - 1 ? kMidSub - 1 : sub);
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
       b[q] = off[v];
       const int64_t dd = off[v + 1] - b[q];
       d[q] = (int)dd;  // rows above INT32_MAX are refused after binning
-      key[q] = window_key(dd, e0, lmax);
+      key[q] = window_key(dd, b[q], e0, lmax);
       atomicAdd(&s_hist[key[q]], 1);
     }
   }

@@ -47,12 +47,9 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
 }
 
 // Hub sweep: CTA c sweeps hub c, one leaf per thread, leaves merged by shuffles within
-// warps and through shared memory across warps.  RUNS folds runs of equal consecutive
-// labels as one add (MG only; the caller enables it when every sum of a row's weights is
-// exact in fp32, so the bits do not change).
-template <class S, bool WT, bool RUNS, bool RESCAN = false>
+// warps and through shared memory across warps.
+template <class S, bool WT, bool RESCAN = false>
 __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPlan p) {
-  constexpr bool kRuns = RUNS && S::kRunMergeable && !RESCAN;
   if (a.done != nullptr && *a.done) return;
   __shared__ int sk[(kThreads / 32) * 32];
   __shared__ float sv[(kThreads / 32) * 32];
@@ -70,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   S st;
   st.init(own);
   if (tid < L)
-    fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
+    fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
                                    base + ((tid + 1) * d) / L);
   const int Lw = L < 32 ? L : 32;
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
@@ -138,9 +135,8 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
 // mid vertex whose L lanes are aligned inside the warp).  Lanes of one warp may belong to
 // vertices of different L: every lane runs the warp's largest L, merging only below its
 // own.  Warps are independent, so a CTA of kLaneThreads holds as few of them as possible.
-template <class S, bool WT, bool RUNS, bool RESCAN = false>
+template <class S, bool WT, bool RESCAN = false>
 __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
-  constexpr bool kRuns = RUNS && S::kRunMergeable && !RESCAN;
   if (a.done != nullptr && *a.done) return;
   const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -162,7 +158,7 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
   if (v >= 0) {
     own = a.c_prev[v];
     st.init(own);
-    if (act) fold_range<S, WT, true, kRuns>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
+    if (act) fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
   } else {
     st.init(-1);
   }
@@ -217,19 +213,27 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
 // One sweep: the hub kernel on s_hub and the lane kernel on s (the caller orders the two
 // streams; they may be the same stream).  Both write disjoint entries of c_next and add to
 // the same dN counters.
-template <class S, bool WT, bool RUNS, bool RESCAN = false>
+template <class S, bool WT, bool RESCAN = false>
 cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
                                cudaStream_t s_hub) {
   if (p.nhubs > 0) {
-    sweep_hub_kernel<S, WT, RUNS, RESCAN><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
+    sweep_hub_kernel<S, WT, RESCAN><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
     count_launch();
   }
   const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
   if (lane_ctas > 0) {
-    sweep_lane_kernel<S, WT, RUNS, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    sweep_lane_kernel<S, WT, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
     count_launch();
   }
   return cudaGetLastError();
+}
+
+// The two instantiations of one sketch type: weighted or not.
+template <class S>
+cudaError_t launch_warp_variants(bool weighted, const SweepArgs& a, const WarpPlan& p,
+                                 cudaStream_t s, cudaStream_t s_hub) {
+  return weighted ? launch_warp_kernel<S, true>(a, p, s, s_hub)
+                  : launch_warp_kernel<S, false>(a, p, s, s_hub);
 }
 
 // The MG ablation variants of one k: paper-literal accumulate and / or double scan.
@@ -238,24 +242,13 @@ cudaError_t launch_mg_variant(bool literal, bool rescan, bool weighted, const Sw
                               const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
   if (literal) {
     if (rescan)
-      return weighted ? launch_warp_kernel<MGLiteral<K>, true, false, true>(a, p, s, s_hub)
-                      : launch_warp_kernel<MGLiteral<K>, false, false, true>(a, p, s, s_hub);
-    return weighted ? launch_warp_kernel<MGLiteral<K>, true, false, false>(a, p, s, s_hub)
-                    : launch_warp_kernel<MGLiteral<K>, false, false, false>(a, p, s, s_hub);
+      return weighted ? launch_warp_kernel<MGLiteral<K>, true, true>(a, p, s, s_hub)
+                      : launch_warp_kernel<MGLiteral<K>, false, true>(a, p, s, s_hub);
+    return weighted ? launch_warp_kernel<MGLiteral<K>, true, false>(a, p, s, s_hub)
+                    : launch_warp_kernel<MGLiteral<K>, false, false>(a, p, s, s_hub);
   }
-  return weighted ? launch_warp_kernel<MGSketch<K>, true, false, true>(a, p, s, s_hub)
-                  : launch_warp_kernel<MGSketch<K>, false, false, true>(a, p, s, s_hub);
-}
-
-// The four instantiations of one sketch type: weighted or not, runs folded or not.
-template <class S>
-cudaError_t launch_warp_variants(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
-                                 cudaStream_t s, cudaStream_t s_hub) {
-  if (weighted)
-    return runs ? launch_warp_kernel<S, true, true>(a, p, s, s_hub)
-                : launch_warp_kernel<S, true, false>(a, p, s, s_hub);
-  return runs ? launch_warp_kernel<S, false, true>(a, p, s, s_hub)
-              : launch_warp_kernel<S, false, false>(a, p, s, s_hub);
+  return weighted ? launch_warp_kernel<MGSketch<K>, true, true>(a, p, s, s_hub)
+                  : launch_warp_kernel<MGSketch<K>, false, true>(a, p, s, s_hub);
 }
 
 }  // namespace lpa

@@ -3,9 +3,9 @@
 
 namespace lpa {
 
-cudaError_t launch_sweep_mg16(bool weighted, bool runs, const SweepArgs& a, const WarpPlan& p,
+cudaError_t launch_sweep_mg16(bool weighted, const SweepArgs& a, const WarpPlan& p,
                               cudaStream_t s, cudaStream_t s_hub) {
-  return launch_warp_variants<MGSketch<16>>(weighted, runs, a, p, s, s_hub);
+  return launch_warp_variants<MGSketch<16>>(weighted, a, p, s, s_hub);
 }
 
 }  // namespace lpa
