@@ -105,9 +105,9 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int64_t tab_slots) {
     L.lane_cap = lane_cap(n, m, e0);
     L.desc = take(sizeof(int4) * (size_t)(nwin * kWinVerts));
     L.wtab = take(sizeof(int32_t) * (size_t)(nwin * kWinTab));
-    L.hcnt = take(sizeof(int32_t) * (size_t)nwin);
+    L.hcnt = take(sizeof(int32_t) * (size_t)(kHubClasses * nwin));
     L.lcnt = take(sizeof(int32_t) * (size_t)nwin);
-    L.hub_prefix = take(sizeof(int64_t) * (size_t)(nwin + 1));
+    L.hub_prefix = take(sizeof(int64_t) * (size_t)(kHubClasses * nwin + 1));
     L.lane_prefix = take(sizeof(int64_t) * (size_t)(nwin + 1));
     L.hub_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.hub_cap, 1));
     L.lane_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.lane_cap, 1));
@@ -276,7 +276,7 @@ lpa_status bin_classes(lpa_plan_s* p) {
   LPA_CUDA(launch_fill_u64(counts, 0ull, 8, s));
   LPA_CUDA(launch_fill_u64(counts, 1ull, 1, s));  // profile: all integral until shown otherwise
   LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, desc, wtab, hcnt, lcnt, s));
-  LPA_CUDA(launch_scan_counts(hcnt, nwin, hub_prefix, s));
+  LPA_CUDA(launch_scan_counts(hcnt, (int64_t)kHubClasses * nwin, hub_prefix, s));
   LPA_CUDA(launch_scan_counts(lcnt, nwin, lane_prefix, s));
   LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, (int4*)wp.hub_desc,
                                ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
@@ -284,8 +284,11 @@ lpa_status bin_classes(lpa_plan_s* p) {
   LPA_CUDA(launch_weight_profile(p->off, nullptr, n, p->m, counts, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 3,
                            cudaMemcpyDeviceToHost, s));
-  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 3, hub_prefix + nwin, sizeof(int64_t),
-                           cudaMemcpyDeviceToHost, s));
+  for (int c = 0; c <= kHubClasses; ++c)  // first hub of each class, then the total
+    LPA_CUDA(cudaMemcpyAsync(p->host_cls + 8 + c, hub_prefix + (int64_t)c * nwin,
+                             sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 3, hub_prefix + (int64_t)kHubClasses * nwin,
+                           sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls + 4, lane_prefix + nwin, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
@@ -298,6 +301,7 @@ lpa_status bin_classes(lpa_plan_s* p) {
   const int64_t nctas = nhubs + (nlanes + kThreads - 1) / kThreads;
   if (nctas > 0x7fffffffLL) return fail(LPA_EUNSUPPORTED, "graph too large for one launch grid");
   wp.nhubs = (int32_t)nhubs;
+  for (int c = 0; c <= kHubClasses; ++c) wp.hub_start[c] = (int32_t)p->host_cls[8 + c];
   wp.nlanes = nlanes;
   wp.nctas = (int32_t)nctas;
   p->nhubs = nhubs;

@@ -41,15 +41,20 @@ constexpr int kLowKeys = 1024;         // low-row sort keys (degree, capped)
 constexpr int kMidSub = 4;             // leaf-length quarters per leaf count
 constexpr int kMidClasses = 5 * kMidSub;
 constexpr int kLaneGroups = kMidClasses + 1;  // mid classes, then the low rows
-constexpr int kSortKeys = 1 + kMidClasses + kLowKeys;
+// Hubs are grouped by their CTA size, max(32, L) = 256 >> c for class c, so a hub of 64
+// leaves runs in a 64-thread CTA instead of idling three quarters of a 256-thread one.
+constexpr int kHubClasses = 4;
+constexpr int kSortKeys = kHubClasses + kMidClasses + kLowKeys;
 constexpr int kHubDegree = 4096;
 // Per-window table (kWinTab int32): [0] hub count; [kTabLane + g] first lane of lane group
-// g; [kTabLanes] lanes in use; [kTabVert + g] window slot of group g's first vertex.
+// g; [kTabLanes] lanes in use; [kTabVert + g] window slot of group g's first vertex;
+// [kTabHub + c] window slot of hub class c's first hub.
 constexpr int kTabLane = 1;
 constexpr int kTabLanes = kTabLane + kLaneGroups;
 constexpr int kTabVert = 24;
-constexpr int kWinTab = 48;
-static_assert(kTabLanes < kTabVert && kTabVert + kLaneGroups <= kWinTab, "window table layout");
+constexpr int kTabHub = kTabVert + kLaneGroups;
+constexpr int kWinTab = 52;
+static_assert(kTabLanes < kTabVert && kTabHub + kHubClasses <= kWinTab, "window table layout");
 // Lane descriptor word w: leaf length (< 2^13, rows of a lane have <= kHubDegree
 // positions), leaf index, log2 of the vertex's leaf count.
 constexpr int kLaneLeafShift = 13;
@@ -93,11 +98,12 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
 
 // Binned graph as the warp-per-row kernels see it.
 struct WarpPlan {
-  const int4* hub_desc;   // per hub: {v, offset lo, offset hi, degree}
+  const int4* hub_desc;   // per hub: {v, offset lo, offset hi, degree}, grouped by class
   const int4* lane_desc;  // per lane (see kLaneLeafShift); v = -1 on padding lanes
   int64_t nlanes;         // a multiple of 32
   int32_t nhubs;
   int32_t nctas;          // nhubs + ceil(nlanes / kThreads)
+  int32_t hub_start[kHubClasses + 1];  // first hub of each class; [kHubClasses] = nhubs
 };
 
 // Arguments of one sweep launch.
@@ -191,13 +197,14 @@ cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n,
 cudaError_t launch_sweep_exact(bool weighted, const SweepArgs& a, cudaStream_t s);
 size_t exact_smem_bytes(bool weighted);
 // Binning for the warp-per-row kernels.  Per window: sort the vertices into groups, write
-// their descriptors, the window table, the hub count and the padded lane count.
+// their descriptors, the window table, the hub count of each class (class-major:
+// hcnt[c * nwin + window]) and the padded lane count.
 cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int4* desc,
                                int32_t* wtab, int32_t* hcnt, int32_t* lcnt, cudaStream_t s);
 // prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s);
-// Hub and lane descriptors of every window at their prefix offsets (capacities bound the
-// writes).
+// Hub and lane descriptors of every window at their prefix offsets (hub_prefix over the
+// class-major hub counts; capacities bound the writes).
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
                                 const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
                                 int64_t hub_cap, int4* lane_desc, int64_t lane_cap,

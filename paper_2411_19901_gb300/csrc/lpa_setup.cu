@@ -177,22 +177,24 @@ __global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t
 
 // ------------------------------------------------- binning for the warp sweep
 
-// Sort key of a vertex with d positions starting at CSR position b inside its window: 0
-// hub; 1 + c for mid class c (larger L and longer leaves first); for a one-leaf row
-// 1 + kMidClasses + (kLowKeys - 1 - min(a, kLowKeys - 1)) with a = d + (b mod 4), the
+// Sort key of a vertex with d positions starting at CSR position b inside its window: its
+// class c < kHubClasses for a hub; kHubClasses + c for mid class c (larger L and longer
+// leaves first); for a one-leaf row kHubClasses + kMidClasses + (kLowKeys - 1 -
+// min(a, kLowKeys - 1)) with a = d + (b mod 4), the
 // row's span in 16-byte groups' positions, so the rows of a warp read the same number of
 // aligned groups (longer spans first).
 __device__ __forceinline__ int window_key(int64_t d, int64_t b, int e0, int lmax) {
   const int L = leaf_count(d, e0, lmax);
-  if (d > kHubDegree || L > kMaxWarpLeaves) return 0;
+  if (d > kHubDegree || L > kMaxWarpLeaves)  // hub class c: CTA of 256 >> c threads
+    return L >= 256 ? 0 : (L == 128 ? 1 : (L == 64 ? 2 : 3));
   if (L == 1) {
     const int64_t a = d + (b & 3);
-    return 1 + kMidClasses + (kLowKeys - 1 - (int)(a < kLowKeys ? a : kLowKeys - 1));
+    return kHubClasses + kMidClasses + (kLowKeys - 1 - (int)(a < kLowKeys ? a : kLowKeys - 1));
   }
   const int lidx = 5 - (31 - __clz(L));  // L = 32 -> 0 ... L = 2 -> 4
   int sub = (int)(((d / L) * 4) / e0) - 4;  // leaf length quarter in [e0, 2 e0)
   sub = sub < 0 ? 0 : (sub > kMidSub - 1 ? kMidSub - 1 : sub);
-  return 1 + lidx * kMidSub + (kMidSub - 1 - sub);
+  return kHubClasses + lidx * kMidSub + (kMidSub - 1 - sub);
 }
 
 constexpr int kSortThreads = 1024;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
     int32_t* lcnt) {
   __shared__ int s_hist[kSortPad];
   __shared__ int s_wsum[kSortThreads / 32];
-  __shared__ int s_grp[1 + kLaneGroups];  // hubs, mid classes, low rows
+  __shared__ int s_grp[kHubClasses + kLaneGroups];  // hub classes, mid classes, low rows
   constexpr int kPer = kWinVerts / kSortThreads;
   const int tid = threadIdx.x;
   for (int i = tid; i < kSortPad; i += kSortThreads) s_hist[i] = 0;
@@ -230,12 +232,12 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
     }
   }
   __syncthreads();
-  if (tid <= kLaneGroups) {
+  if (tid < kHubClasses + kLaneGroups) {
     int c = 0;
-    if (tid <= kMidClasses) {
+    if (tid < kHubClasses + kMidClasses) {
       c = s_hist[tid];
     } else {
-      for (int k = 1 + kMidClasses; k < kSortKeys; ++k) c += s_hist[k];
+      for (int k = kHubClasses + kMidClasses; k < kSortKeys; ++k) c += s_hist[k];
     }
     s_grp[tid] = c;
   }
@@ -256,18 +258,22 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
   s_hist[2 * tid + 1] = ex + x0;
   if (tid == 0) {
     int32_t* t = wtab + (int64_t)blockIdx.x * kWinTab;
-    const int nh = s_grp[0];
+    int nh = 0;
+    for (int c = 0; c < kHubClasses; ++c) {
+      t[kTabHub + c] = nh;
+      hcnt[(int64_t)c * gridDim.x + blockIdx.x] = s_grp[c];
+      nh += s_grp[c];
+    }
     int lanes = 0, slot = nh;
     for (int g = 0; g < kLaneGroups; ++g) {
       t[kTabLane + g] = lanes;
       t[kTabVert + g] = slot;
-      const int cnt = s_grp[1 + g];
+      const int cnt = s_grp[kHubClasses + g];
       lanes += cnt * (g < kMidClasses ? 32 >> (g / kMidSub) : 1);
       slot += cnt;
     }
     t[0] = nh;
     t[kTabLanes] = lanes;
-    hcnt[blockIdx.x] = nh;
     lcnt[blockIdx.x] = (lanes + 31) & ~31;
   }
   __syncthreads();
@@ -320,9 +326,12 @@ __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
   __syncthreads();
   const int4* wd = desc + win * kWinVerts;
   const int nh = t[0];
-  const int64_t h0 = hub_prefix[win];
-  for (int i = tid; i < nh; i += kSortThreads)
-    if (h0 + i < hub_cap) hub_desc[h0 + i] = wd[i];
+  for (int i = tid; i < nh; i += kSortThreads) {
+    int c = kHubClasses - 1;  // the class whose slots hold i
+    while (c > 0 && t[kTabHub + c] > i) --c;
+    const int64_t pos = hub_prefix[(int64_t)c * gridDim.x + win] + (i - t[kTabHub + c]);
+    if (pos < hub_cap) hub_desc[pos] = wd[i];
+  }
   const int lanes = t[kTabLanes];
   const int64_t l0 = lane_prefix[win];
   const int padded = (int)(lane_prefix[win + 1] - l0);

@@ -47,7 +47,8 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
 }
 
 // Hub sweep: CTA c sweeps hub c, one leaf per thread, leaves merged by shuffles within
-// warps and through shared memory across warps.
+// warps and through shared memory across warps.  Launched per hub class with CTAs of
+// max(32, L) threads, so every warp of a CTA holds leaves.
 template <class S, bool WT, bool RESCAN = false>
 __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPlan p) {
   if (a.done != nullptr && *a.done) return;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   if (a.act_out != nullptr) {  // a moved vertex marks its neighbours unprocessed
     __syncthreads();
     if (s_changed)
-      for (int64_t q = base + tid; q < base + d; q += kThreads) a.act_out[__ldg(a.idx + q)] = 1;
+      for (int64_t q = base + tid; q < base + d; q += blockDim.x) a.act_out[__ldg(a.idx + q)] = 1;
   }
 }
 
@@ -216,8 +217,12 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
 template <class S, bool WT, bool RESCAN = false>
 cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
                                cudaStream_t s_hub) {
-  if (p.nhubs > 0) {
-    sweep_hub_kernel<S, WT, RESCAN><<<(unsigned)p.nhubs, kThreads, 0, s_hub>>>(a, p);
+  for (int c = 0; c < kHubClasses; ++c) {  // one launch per hub class, CTAs of 256 >> c
+    const int cnt = p.hub_start[c + 1] - p.hub_start[c];
+    if (cnt <= 0) continue;
+    WarpPlan q = p;
+    q.hub_desc = p.hub_desc + p.hub_start[c];
+    sweep_hub_kernel<S, WT, RESCAN><<<(unsigned)cnt, kThreads >> c, 0, s_hub>>>(a, q);
     count_launch();
   }
   const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
