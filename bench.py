@@ -42,8 +42,8 @@ UNIT = "edges/s"
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
 # hash of the sweep kernel source it was taken with.  If the source changes, traffic is
 # reported as null until a new capture is taken.
-SWEEP_TRAFFIC = {"src_sha256": "e8f9e7982f1732de8f721328d54116f0cacf86c9ea03ab10fa44a7ec6490d91f", "workload": "lfr26",
-                 "bytes_per_launch": 35120390741}
+SWEEP_TRAFFIC = {"src_sha256": "10acdeaada18eb88d06f0a124e36ff60baf6ef3085504a233ce8394b86f0cc9e", "workload": "lfr26",
+                 "bytes_per_launch": 37306222763}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
