@@ -1,6 +1,6 @@
 // lpa_fold.cuh -- device building blocks of the sweep: the register sketches (weighted
-// Misra-Gries, weighted Boyer-Moore), the pipelined row fold, and the work decomposition
-// over the binned graph (hub CTAs, mid-degree leaf groups, degree-sorted low rows).
+// Misra-Gries as the paper uses it and as printed, weighted Boyer-Moore), the double-scan
+// helpers and the pipelined row fold.
 #pragma once
 
 #include "lpa_internal.cuh"
@@ -410,43 +410,6 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
     LPA_STEP(X2, W2, X0, W0, X1, W1)
   }
 #undef LPA_STEP
-}
-
-// ------------------------------------------------------------ work decomposition
-
-// Work map over a binned graph for kernels of kThreads-thread CTAs (modularity): CTA c <
-// nhubs takes hub c whole; the following CTAs take the packed lanes in order, one lane
-// descriptor per thread.
-struct Work {
-  int kind;    // 0 hub (the whole CTA), 1 a lane of a mid or low vertex
-  int v;       // vertex (or -1 for an idle lane)
-  int leaf;    // leaf index of this lane, 0 for a hub
-  int L;       // leaves of the vertex (1 for low rows and idle lanes; hubs: unused)
-  int64_t b;   // hub: row start and length; lane: its leaf's start and length
-  int64_t d;
-};
-
-// The work of thread tid of CTA cta: a hub CTA, or one lane of the packed mid and low
-// vertices.
-__device__ __forceinline__ Work lane_work(const WarpPlan& p, int cta, int tid) {
-  Work w{1, -1, 0, 1, 0, 0};
-  if (cta < p.nhubs) {
-    const int4 h = __ldg(p.hub_desc + cta);
-    w.kind = 0;
-    w.v = h.x;
-    w.b = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
-    w.d = h.w;
-    return w;
-  }
-  const int64_t q = (int64_t)(cta - p.nhubs) * kThreads + tid;
-  if (q >= p.nlanes) return w;
-  const int4 l = __ldg(p.lane_desc + q);
-  w.v = l.x;
-  w.b = (int64_t)(uint32_t)l.y | ((int64_t)l.z << 32);
-  w.d = l.w & ((1 << kLaneLeafShift) - 1);
-  w.leaf = (l.w >> kLaneLeafShift) & 31;
-  w.L = 1 << (l.w >> kLaneLgShift);
-  return w;
 }
 
 }  // namespace lpa

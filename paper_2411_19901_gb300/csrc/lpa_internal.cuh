@@ -102,7 +102,7 @@ struct WarpPlan {
   const int4* lane_desc;  // per lane (see kLaneLeafShift); v = -1 on padding lanes
   int64_t nlanes;         // a multiple of 32
   int32_t nhubs;
-  int32_t nctas;          // nhubs + ceil(nlanes / kThreads)
+  int32_t nctas;          // nhubs + ceil(nlanes / kThreads) (work units, for the stats)
   int32_t hub_start[kHubClasses + 1];  // first hub of each class; [kHubClasses] = nhubs
 };
 

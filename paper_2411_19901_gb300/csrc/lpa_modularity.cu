@@ -1,8 +1,8 @@
 // lpa_modularity.cu -- modularity (Sec. 3.2, Eq. 1) over the binned graph of a run:
 // Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2, accumulated in fp64.
 //
-// The rows pass reuses the sweep's work map (hub CTAs, mid leaf groups, degree-sorted
-// low rows) and its pipelined row reads, so it streams the CSR at the sweep's rate.
+// The rows pass reuses the sweep's work map (hub kernels per CTA-size class, packed lane
+// descriptors) and its pipelined row reads, so it streams the CSR at the sweep's rate.
 // Per vertex it forms K_i (all entries, self-loops included, as stored) and the weight of
 // entries whose neighbour shares the label; Sigma_c receives K_i through one atomic per
 // run of equal labels in a warp.  Block sums go to kModSlots accumulators.
@@ -50,74 +50,27 @@ __device__ __forceinline__ double warp_down_sum(double x, int L, int Lw) {
   return x;
 }
 
-template <bool WT>
-__global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
-    const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
-    const float* __restrict__ wts, int64_t m, const int32_t* __restrict__ labels, WarpPlan p,
-    double* sigma_c, double* slots) {
-  __shared__ double s_k[kThreads], s_in[kThreads];
+// A block's vertex totals: Sigma_c through one atomic per distinct label among a warp's
+// owners, then the block's sums of K_i and of the intra-community weight into one of
+// kModSlots accumulators.  s_k, s_in: blockDim.x doubles of shared memory each.
+__device__ __forceinline__ void mod_commit(bool owner, int cv, double kv, double in,
+                                           double* sigma_c, double* slots, double* s_k,
+                                           double* s_in) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const Work wk = lane_work(p, (int)blockIdx.x, tid);
-  ModAcc acc{0.f, 0.f, 0.f, 0.f, -1};
-  double kv = 0.0, in = 0.0;  // this thread's totals
-  bool owner = false;         // this thread ends holding a vertex total
-  int v = -1;
-  if (wk.kind == 0) {
-    v = wk.v;
-    const int64_t base = wk.b;
-    const int64_t d = wk.d;
-    const int L = leaf_count(d, 1, kThreads);  // split the row over all threads
-    acc.cv = labels[v];
-    if (tid < L)
-      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (tid * d) / L,
-                                    base + ((tid + 1) * d) / L);
-    s_k[tid] = acc.k();
-    s_in[tid] = acc.in();
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {  // fixed-order tree
-      if (tid < s) {
-        s_k[tid] += s_k[tid + s];
-        s_in[tid] += s_in[tid + s];
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      kv = s_k[0];
-      in = s_in[0];
-      owner = true;
-    }
-    __syncthreads();
-  } else {
-    v = wk.v;
-    if (v >= 0) {
-      acc.cv = labels[v];
-      fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, wk.b, wk.b + wk.d);
-    }
-    kv = acc.k();
-    in = acc.in();
-    const int Lw = __reduce_max_sync(kFullMask, wk.L);
-    if (Lw > 1) {
-      kv = warp_down_sum(kv, wk.L, Lw);
-      in = warp_down_sum(in, wk.L, Lw);
-    }
-    owner = v >= 0 && wk.leaf == 0;
-  }
-  // Sigma_c: lanes of one warp with the same label add through their lowest lane
-  const int key = owner ? acc.cv : -(lane + 2);
+  const int key = owner ? cv : -(lane + 2);
   const unsigned grp = __match_any_sync(kFullMask, key);
   s_k[tid] = owner ? kv : 0.0;
   __syncwarp();
   if (owner && lane == __ffs(grp) - 1) {
     double sum = 0.0;
     for (unsigned g = grp; g; g &= g - 1) sum += s_k[(tid & ~31) + __ffs(g) - 1];
-    if (sum != 0.0) atomicAdd(sigma_c + acc.cv, sum);
+    if (sum != 0.0) atomicAdd(sigma_c + cv, sum);
   }
   __syncthreads();
-  // block totals of K_i and of intra-community weight
   s_k[tid] = owner ? kv : 0.0;
   s_in[tid] = owner ? in : 0.0;
   __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (tid < s) {
       s_k[tid] += s_k[tid + s];
       s_in[tid] += s_in[tid + s];
@@ -125,10 +78,72 @@ __global__ void __launch_bounds__(kThreads) modularity_plan_kernel(
     __syncthreads();
   }
   if (tid == 0 && (s_k[0] != 0.0 || s_in[0] != 0.0)) {
-    const int slot = blockIdx.x & (kModSlots - 1);
+    const int slot = (blockIdx.x * 7919u) & (kModSlots - 1);
     atomicAdd(slots + 2 * slot, s_k[0]);
     atomicAdd(slots + 2 * slot + 1, s_in[0]);
   }
+}
+
+// Packed lanes (the sweep's lane descriptors): each lane sums its leaf, the L lanes of a
+// vertex combine by shuffles, the vertex's first lane holds its totals.
+template <bool WT>
+__global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
+    const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
+    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots) {
+  __shared__ double s_k[kLaneThreads], s_in[kLaneThreads];
+  const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
+  int v = -1, leaf = 0, L = 1;
+  int64_t lo = 0, len = 0;
+  if (q < p.nlanes) {
+    const int4 l = __ldg(p.lane_desc + q);
+    v = l.x;
+    lo = (int64_t)(uint32_t)l.y | ((int64_t)l.z << 32);
+    len = l.w & ((1 << kLaneLeafShift) - 1);
+    leaf = (l.w >> kLaneLeafShift) & 31;
+    L = 1 << (l.w >> kLaneLgShift);
+  }
+  ModAcc acc{0.f, 0.f, 0.f, 0.f, -1};
+  if (v >= 0) {
+    acc.cv = labels[v];
+    fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, lo, lo + len);
+  }
+  double kv = acc.k(), in = acc.in();
+  const int Lw = __reduce_max_sync(kFullMask, L);
+  if (Lw > 1) {
+    kv = warp_down_sum(kv, L, Lw);
+    in = warp_down_sum(in, L, Lw);
+  }
+  mod_commit(v >= 0 && leaf == 0, acc.cv, kv, in, sigma_c, slots, s_k, s_in);
+}
+
+// Hubs of one class (p.hub_desc points at the class): the row split evenly over the CTA.
+template <bool WT>
+__global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
+    const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
+    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots) {
+  __shared__ double s_k[kThreads], s_in[kThreads];
+  const int tid = threadIdx.x;
+  const int nt = blockDim.x;
+  const int4 h = __ldg(p.hub_desc + blockIdx.x);
+  const int v = h.x;
+  const int64_t base = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
+  const int64_t d = h.w;
+  ModAcc acc{0.f, 0.f, 0.f, 0.f, labels[v]};
+  fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (tid * d) / nt,
+                                base + ((tid + 1) * d) / nt);
+  s_k[tid] = acc.k();
+  s_in[tid] = acc.in();
+  __syncthreads();
+  for (int s = nt / 2; s > 0; s >>= 1) {  // fixed-order tree
+    if (tid < s) {
+      s_k[tid] += s_k[tid + s];
+      s_in[tid] += s_in[tid + s];
+    }
+    __syncthreads();
+  }
+  const double kv = s_k[0], in = s_in[0];
+  __syncthreads();
+  mod_commit(tid == 0, acc.cv, kv, in, sigma_c, slots, s_k, s_in);
 }
 
 __global__ void zero_f64_kernel(double* p, int64_t count) {
@@ -202,12 +217,26 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
   count_launch();
   zero_f64_kernel<<<16, 256, 0, s>>>(slots, 2 * kModSlots);
   count_launch();
-  const unsigned grid = (unsigned)p.nctas;
-  if (grid > 0) {
+  (void)off;
+  for (int c = 0; c < kHubClasses; ++c) {
+    const int cnt = p.hub_start[c + 1] - p.hub_start[c];
+    if (cnt <= 0) continue;
+    WarpPlan q = p;
+    q.hub_desc = p.hub_desc + p.hub_start[c];
     if (w)
-      modularity_plan_kernel<true><<<grid, kThreads, 0, s>>>(off, idx, w, m, labels, p, sigma_c, slots);
+      modularity_hub_kernel<true><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots);
     else
-      modularity_plan_kernel<false><<<grid, kThreads, 0, s>>>(off, idx, w, m, labels, p, sigma_c, slots);
+      modularity_hub_kernel<false><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots);
+    count_launch();
+  }
+  const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
+  if (lane_ctas > 0) {
+    if (w)
+      modularity_lane_kernel<true><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
+                                                                               sigma_c, slots);
+    else
+      modularity_lane_kernel<false><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
+                                                                                sigma_c, slots);
     count_launch();
   }
   sigma_sq_kernel<<<kSqBlocks, 256, 0, s>>>(sigma_c, n, sq);
