@@ -36,7 +36,7 @@ constexpr int kMaxLeaves = 256;        // largest leaf_max accepted
 // 16-byte descriptor per lane, so a thread finds its work with one load and rows swept at
 // the same time share neighbour-label ranges in L2.  The grid runs every hub first (a CTA
 // each), then the lanes, kThreads to a CTA.
-constexpr int kWinVerts = 4096;
+constexpr int kWinVerts = 16384;
 constexpr int kLowKeys = 1024;         // low-row sort keys (degree, capped)
 constexpr int kMidSub = 4;             // leaf-length quarters per leaf count
 constexpr int kMidClasses = 5 * kMidSub;
