@@ -435,10 +435,22 @@ def run_ours(args):
     sweeps = sum(s["iterations"] for s in stats)
     sweep_ms = sum(s["sweep_ms"] for s in stats)
 
-    # end to end through the host-memory entry point
+    # end to end through the host-memory entry point: one untimed call first (it grows
+    # the library's device pool by the staging buffers), then e2e_steps timed calls, each
+    # with its host-to-device copies and its labels back to host memory
     e2e_steps = max(1, min(args.steps, 3))
     h_lab = torch.empty(n, dtype=torch.int32, pin_memory=pin)
     e2e_stats = []
+
+    def e2e_call():
+        st = lpa.lpa_stats()
+        lpa.lpa_detect_host(h_off.numpy(), h_idx.numpy(), h_w.numpy() if weighted else None,
+                            n, m, args.mode, 8, 0.05, 20, h_lab.numpy(), st,
+                            lpa.make_options(validate=False, modularity=True, stream=stream,
+                                             workspace=ws))
+        return st.to_dict()
+
+    e2e_call()
     torch.cuda.synchronize(dev)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -446,12 +458,7 @@ def run_ours(args):
     t_host = time.perf_counter()
     e0.record(stream)
     for _ in range(e2e_steps):
-        st = lpa.lpa_stats()
-        lpa.lpa_detect_host(h_off.numpy(), h_idx.numpy(), h_w.numpy() if weighted else None,
-                            n, m, args.mode, 8, 0.05, 20, h_lab.numpy(), st,
-                            lpa.make_options(validate=False, modularity=True, stream=stream,
-                                             workspace=ws))
-        e2e_stats.append(st.to_dict())
+        e2e_stats.append(e2e_call())
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))

@@ -285,6 +285,13 @@ lpa_status lpa_server_drain(lpa_server server, uint64_t* tickets, int32_t cap, i
 /* Frees the server; requests not yet done are dropped (their outputs unspecified). */
 lpa_status lpa_server_destroy(lpa_server server);
 
+/* ---- Memory. ------------------------------------------------------------------------
+ * Device memory the library allocates (plan workspaces, lpa_detect_host staging, batch
+ * and server arenas) comes from one stream-ordered pool per device that keeps freed
+ * memory for later calls instead of returning it to the driver.  lpa_release_memory
+ * returns every unused byte of those pools (memory of live plans and servers stays). */
+lpa_status lpa_release_memory(void);
+
 const char* lpa_status_string(lpa_status s);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* lpa_last_error(void);

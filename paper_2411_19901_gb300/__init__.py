@@ -8,6 +8,6 @@ from .lpa import (  # noqa: F401
     LPA_TIMING, LPA_VALIDATE, LpaError, Plan, Server, detect,
     lpa_batch_detect, lpa_detect, lpa_detect_ex, lpa_detect_host, lpa_launch_count, lpa_modularity, lpa_modularity_ex,
     lpa_modularity_workspace_size, lpa_options, lpa_options_init, lpa_plan_create,
-    lpa_plan_destroy, lpa_plan_run, lpa_plan_sweep, lpa_stats, lpa_version,
+    lpa_plan_destroy, lpa_plan_run, lpa_plan_sweep, lpa_release_memory, lpa_stats, lpa_version,
     lpa_workspace_size, lpa_workspace_size_ex, make_options, modularity,
 )

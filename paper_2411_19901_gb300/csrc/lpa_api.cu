@@ -8,6 +8,8 @@
 // the exact mode runs its chunk kernel over the chunk/hub binning.
 #include <algorithm>
 #include <chrono>
+#include <cstdint>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +49,47 @@ lpa_status fail(lpa_status s, const char* fmt, ...) {
   } while (0)
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device memory of the library comes from one stream-ordered pool per device that keeps
+// freed memory for the next call (release threshold: unlimited), so repeated calls do
+// not map and unmap gigabytes of pages each time.  lpa_release_memory() trims the pools.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t lib_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+// Stream-ordered allocation from the library's pool (free with cudaFreeAsync).
+cudaError_t lib_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  cudaError_t e = lib_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
 
 int64_t num_windows(int64_t n) { return (n + kWinVerts - 1) / kWinVerts; }
 
@@ -349,7 +392,7 @@ lpa_status bin_chunks(lpa_plan_s* p, const lpa_options& o) {
       p->tab_vals = (float*)(p->ws + p->lay.tab_vals);
     } else {
       const size_t kb = align256(sizeof(int32_t) * (size_t)slots);
-      LPA_CUDA(cudaMallocAsync((void**)&p->tab_ws, kb + sizeof(float) * (size_t)slots, s));
+      LPA_CUDA(lib_alloc((void**)&p->tab_ws, kb + sizeof(float) * (size_t)slots, s));
       p->own_tab = true;
       p->tab_keys = (int32_t*)p->tab_ws;
       p->tab_vals = (float*)(p->tab_ws + kb);
@@ -418,9 +461,9 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
     p->ws_bytes = o.workspace_bytes;
   } else {
     p->ws_bytes = p->lay.total_fixed;
-    ce = cudaMallocAsync((void**)&p->ws, p->ws_bytes, p->stream);
+    ce = lib_alloc((void**)&p->ws, p->ws_bytes, p->stream);
     if (ce != cudaSuccess)
-      return bail(fail(LPA_ENOMEM, "cudaMallocAsync(%zu): %s", p->ws_bytes, cudaGetErrorString(ce)));
+      return bail(fail(LPA_ENOMEM, "device allocation of %zu bytes: %s", p->ws_bytes, cudaGetErrorString(ce)));
     p->own_ws = true;
   }
   p->st = (DevState*)(p->ws + p->lay.state);
@@ -738,7 +781,7 @@ lpa_status alloc_packing(Packing& P, int gcap, int64_t ncap, int64_t mcap, bool 
                o_gid = take(4 * (size_t)ncap + 4), o_st = take(4 * 5 * (size_t)gcap),
                o_gdn = take(4 * (size_t)gcap), o_l0 = take(4 * (size_t)ncap + 4),
                o_l1 = take(4 * (size_t)ncap + 4);
-  LPA_CUDA(cudaMallocAsync((void**)&P.dev, at, s));
+  LPA_CUDA(lib_alloc((void**)&P.dev, at, s));
   P.tab = (BatchGraph*)(P.dev + o_tab);
   P.bases = (int64_t*)(P.dev + o_b);
   P.old_vb = (int64_t*)(P.dev + o_ovb);
@@ -1081,7 +1124,7 @@ lpa_status lpa_detect_host(const int64_t* offsets, const int32_t* indices, const
   const size_t b_idx = align256(sizeof(int32_t) * (size_t)m);
   const size_t b_w = weights ? align256(sizeof(float) * (size_t)m) : 0;
   const size_t b_lab = align256(sizeof(int32_t) * (size_t)n);
-  LPA_CUDA(cudaMallocAsync((void**)&dev, b_off + b_idx + b_w + b_lab, st));
+  LPA_CUDA(lib_alloc((void**)&dev, b_off + b_idx + b_w + b_lab, st));
   int64_t* d_off = (int64_t*)dev;
   int32_t* d_idx = (int32_t*)(dev + b_off);
   float* d_w = weights ? (float*)(dev + b_off + b_idx) : nullptr;
@@ -1128,7 +1171,7 @@ lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices, con
     if (o.workspace_bytes < need) return fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, need);
     if (((uintptr_t)ws & 255) != 0) return fail(LPA_EINVAL, "workspace is not 256-byte aligned");
   } else {
-    LPA_CUDA(cudaMallocAsync((void**)&ws, need, st));
+    LPA_CUDA(lib_alloc((void**)&ws, need, st));
     own = true;
   }
   double* sigma_c = (double*)ws;
@@ -1227,7 +1270,7 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
                o_gid = take(4 * (size_t)N), o_state = take(4 * (3 * (size_t)count + 2)),
                o_gdn = take(4 * (size_t)max_iter * count + 4), o_lab = take(4 * (size_t)N + 4);
   char* dev = nullptr;
-  LPA_CUDA(cudaMallocAsync((void**)&dev, at, s));
+  LPA_CUDA(lib_alloc((void**)&dev, at, s));
   auto cleanup = [&](lpa_status st) {
     cudaFreeAsync(dev, s);
     cudaStreamSynchronize(s);
@@ -1330,7 +1373,7 @@ lpa_status lpa_server_create(lpa_mode mode, int32_t k, double tol, int32_t max_i
   S->opt = o;
   S->stream = (cudaStream_t)o.stream;
   S->budget = hbm_budget_bytes;
-  cudaError_t ce = cudaMallocAsync((void**)&S->d_err, 256, S->stream);
+  cudaError_t ce = lib_alloc((void**)&S->d_err, 256, S->stream);
   if (ce != cudaSuccess) {
     delete S;
     return fail(LPA_ENOMEM, "server scratch: %s", cudaGetErrorString(ce));
@@ -1410,6 +1453,16 @@ lpa_status lpa_server_drain(lpa_server S, uint64_t* tickets, int32_t cap, int32_
   for (int32_t i = 0; i < c; ++i) tickets[i] = S->finished[i];
   S->finished.erase(S->finished.begin(), S->finished.begin() + c);
   *count = c;
+  return LPA_OK;
+}
+
+lpa_status lpa_release_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < kMaxDevices; ++d)
+    if (g_pools[d]) {
+      cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+      if (e != cudaSuccess) return fail(LPA_ECUDA, "cudaMemPoolTrimTo: %s", cudaGetErrorString(e));
+    }
   return LPA_OK;
 }
 

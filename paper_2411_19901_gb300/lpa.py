@@ -135,6 +135,7 @@ _SIG = {
     "lpa_server_step": (ctypes.c_int, [_P, _P]),
     "lpa_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P]),
     "lpa_server_drain": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "lpa_release_memory": (ctypes.c_int, []),
     "lpa_server_destroy": (ctypes.c_int, [_P]),
     "lpa_plan_create": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_void_p)]),
@@ -392,6 +393,11 @@ def lpa_batch_detect(graphs, mode="mg", k=8, tol=0.05, max_iter=20,
     out = [{"iterations": int(stats[g].iterations), "converged": bool(stats[g].converged),
             "edges_scanned": int(stats[g].edges_scanned)} for g in range(count)]
     return out, changed[:count, :max_iter]
+
+
+def lpa_release_memory() -> None:
+    """Return the unused device memory of the library's pools to the driver."""
+    _check(load().lpa_release_memory())
 
 
 class Server:

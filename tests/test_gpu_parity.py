@@ -277,3 +277,17 @@ def test_workspace_stream_warm_start_and_host_entry(lpa):
                         stats, lpa.make_options())
     assert np.array_equal(out, ref["labels"])
     assert stats.to_dict()["changed"] == ref["changed"].tolist()
+
+
+def test_memory_pool_release_and_reuse(lpa):
+    """Pool-backed allocations survive a release between calls: results stay exact."""
+    g = synth.random_graph(5000, 10, seed=21, wmax=4, power=2.2, hubs=[(3, 4200)])
+    off, idx, w = to_dev(g)
+    ref = oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG)
+    for _ in range(2):
+        labels, _ = lpa.detect(off, idx, w, mode="mg")
+        assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+        lpa.lpa_release_memory()
+    h = np.empty(g.n, dtype=np.int32)
+    lpa.lpa_detect_host(g.offsets, g.indices, g.weights, g.n, g.m, "mg", 8, 0.05, 20, h)
+    assert np.array_equal(h, ref["labels"])
