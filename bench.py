@@ -271,6 +271,25 @@ def oracle_batch_rate(gs, mode: str, seconds: float):
     return done / dt, done, dt, threads
 
 
+def oracle_serve_latencies(gpool, mode: str, seconds: float):
+    """Requests drawn as in the served workload, each a full oracle run on all host cores,
+    one at a time with no queueing; returns the per-request times (ms) and the threads."""
+    import oracle
+
+    rng = np.random.default_rng(12345)
+    threads = os.cpu_count() or 1
+    om = {"mg": oracle.MG, "bm": oracle.BM, "exact": oracle.EXACT}[mode]
+    lat = []
+    t0 = time.perf_counter()
+    while not lat or time.perf_counter() - t0 < seconds:
+        j = int(512 + rng.integers(0, 8)) if rng.random() < 0.05 else int(rng.integers(0, 512))
+        g = gpool[j]
+        t = time.perf_counter()
+        oracle.lpa(g.offsets, g.indices, g.weights, mode=om, threads=threads)
+        lat.append(1e3 * (time.perf_counter() - t))
+    return lat, threads
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -300,21 +319,9 @@ def run_reference(args):
     if args.workload == "serve":
         import multiprocessing as mp
 
-        import oracle
-
         with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
             gpool = pool.map(_gen_serve, range(520), chunksize=4)
-        rng = np.random.default_rng(12345)
-        threads = os.cpu_count() or 1
-        lat = []
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < 10.0 * max(args.steps, 1) / 5 + 5.0:
-            j = int(512 + rng.integers(0, 8)) if rng.random() < 0.05 else int(rng.integers(0, 512))
-            g = gpool[j]
-            t = time.perf_counter()
-            oracle.lpa(g.offsets, g.indices, g.weights, mode={"mg": oracle.MG, "bm": oracle.BM,
-                       "exact": oracle.EXACT}[args.mode], threads=threads)
-            lat.append(1e3 * (time.perf_counter() - t))
+        lat, threads = oracle_serve_latencies(gpool, args.mode, 10.0 * max(args.steps, 1) / 5 + 5.0)
         p99 = float(np.percentile(lat, 99))
         print(json.dumps({
             "impl": "reference", "metric": SERVE_METRIC, "value": p99, "unit": "ms",
@@ -776,6 +783,13 @@ def run_serve(args):
     if rank != 0:
         return
     entries = np.array([gpool[j].m for j in pick])
+    cpu = None
+    if world == 1:
+        olat, threads = oracle_serve_latencies(gpool, args.mode, 10.0)
+        cpu = {"value": float(np.percentile(olat, 99)), "unit": "ms", "cores": threads,
+               "kind": "oracle",
+               "sample": f"{len(olat)} requests from the same pool, each a full oracle run on "
+                         "all host cores, served one at a time with no queueing"}
     line = {
         "metric": SERVE_METRIC, "value": float(np.percentile(lat, 99)), "unit": "ms",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -793,7 +807,7 @@ def run_serve(args):
         "server_steps": steps, "step_ms_mean": 1e3 * step_time / max(steps, 1),
         "in_flight_mean": inflight_sum / max(steps, 1),
         "bit_equal_sampled": equal, "sampled": len(outputs),
-        "roofline": None, "cpu_baseline": None,
+        "roofline": None, "cpu_baseline": cpu,
         "e2e": {"value": float(np.percentile(lat, 99)), "unit": "ms",
                 "h2d_bytes_per_step": int(sum(8 * (gpool[j].n + 1) + 4 * gpool[j].m
                                              for j in pick[n_warm:]) / max(args.steps, 1)),
