@@ -225,7 +225,9 @@ lpa_status lpa_plan_destroy(lpa_plan plan);
  * lpa_graph, stats and changed_out are HOST memory.  The call allocates its packed copy
  * of the graphs (about 12 B per CSR entry + 40 B per vertex) and frees it before
  * returning; opt->workspace and opt->labels_in are not used (labels_in must be NULL);
- * LPA_TIMING and LPA_MODULARITY are ignored; LPA_VALIDATE checks every graph. */
+ * LPA_TIMING is ignored; LPA_VALIDATE checks every graph; LPA_MODULARITY fills each
+ * graph's modularity (Eq. 1) in stats (sketch modes; with LPA_EXACT it is
+ * LPA_EUNSUPPORTED). */
 typedef struct {
   const int64_t* offsets;  /* device, n + 1 */
   const int32_t* indices;  /* device, m; 16-byte alignment not required here */
@@ -239,6 +241,7 @@ typedef struct {
   int32_t iterations;      /* sweeps the graph took part in */
   int32_t converged;       /* 1 if its own dN/N < tol stopped it */
   int64_t edges_scanned;   /* iterations * m, or -1 with LPA_PRUNE (not tracked per graph) */
+  double modularity;       /* Q of the graph's labels with LPA_MODULARITY, else 0 */
 } lpa_graph_stats;
 
 /* stats: count entries or NULL; changed_out: count * max_iter entries (graph-major: the

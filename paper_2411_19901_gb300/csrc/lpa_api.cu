@@ -1268,7 +1268,8 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
                o_eb = take(8 * (size_t)(count + 1)), o_off = take(8 * (size_t)(N + 1)),
                o_idx = take(4 * (size_t)M), o_w = weighted ? take(4 * (size_t)M) : 0,
                o_gid = take(4 * (size_t)N), o_state = take(4 * (3 * (size_t)count + 2)),
-               o_gdn = take(4 * (size_t)max_iter * count + 4), o_lab = take(4 * (size_t)N + 4);
+               o_gdn = take(4 * (size_t)max_iter * count + 4), o_lab = take(4 * (size_t)N + 4),
+               o_q = take(8 * 3 * (size_t)count);  // per graph: 2m, intra weight, Q
   char* dev = nullptr;
   LPA_CUDA(lib_alloc((void**)&dev, at, s));
   auto cleanup = [&](lpa_status st) {
@@ -1317,14 +1318,36 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
   po.workspace_bytes = 0;
   lpa_plan_s* p = nullptr;
   lpa_status st = plan_create(d_off, d_idx, d_w, (int32_t)N, M, mode, k, &po, &p);
+  if (st == LPA_OK && mode == LPA_EXACT && (o.flags & LPA_MODULARITY)) {
+    destroy_plan(p);
+    return cleanup(fail(LPA_EUNSUPPORTED, "LPA_MODULARITY in a batch needs a sketch mode"));
+  }
   if (st != LPA_OK) return cleanup(st);
   st = batch_run(p, b, tol, max_iter);
+  const bool want_q = (o.flags & LPA_MODULARITY) != 0;
+  double* d_q = (double*)(dev + o_q);
+  if (st == LPA_OK && want_q && N > 0) {  // Eq. 1 per graph on the packed final labels
+    ce = cudaMemsetAsync(d_q, 0, 8 * 2 * (size_t)count, s);
+    if (ce == cudaSuccess)
+      ce = launch_modularity_plan(p->off, p->idx, p->w, p->m, b.labels, p->n, p->wp,
+                                  (double*)(p->ws + p->lay.sigma), (double*)(p->ws + p->lay.partials),
+                                  modularity_plan_partials(p->wp, p->n),
+                                  (double*)(p->ws + p->lay.out4), s, d_gid, d_q, d_q + count);
+    if (ce == cudaSuccess)
+      ce = launch_batch_q(d_tab, count, (double*)(p->ws + p->lay.sigma), d_q, d_q + count,
+                          d_q + 2 * (size_t)count, s);
+    if (ce != cudaSuccess) st = fail(LPA_ECUDA, "batch modularity: %s", cudaGetErrorString(ce));
+  }
   std::vector<int32_t> h_state(3 * (size_t)count);
+  std::vector<double> h_q(want_q ? (size_t)count : 0);
   std::vector<uint32_t> h_gdn((size_t)max_iter * count);
   if (st == LPA_OK) {
     ce = cudaMemcpyAsync(h_state.data(), d_state, 4 * 3 * (size_t)count, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess && changed_out && max_iter > 0)
       ce = cudaMemcpyAsync(h_gdn.data(), b.gdn, 4 * (size_t)max_iter * count,
+                           cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && want_q && N > 0)
+      ce = cudaMemcpyAsync(h_q.data(), d_q + 2 * (size_t)count, 8 * (size_t)count,
                            cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) st = fail(LPA_ECUDA, "batch results: %s", cudaGetErrorString(ce));
@@ -1338,6 +1361,7 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
       stats[g].iterations = it;
       stats[g].converged = h_state[2 * (size_t)count + g];
       stats[g].edges_scanned = prune ? -1 : (int64_t)it * graphs[g].m;
+      stats[g].modularity = (want_q && N > 0) ? h_q[g] : 0.0;
     }
     if (changed_out)
       for (int l = 0; l < max_iter; ++l)
@@ -1439,6 +1463,7 @@ lpa_status lpa_server_poll(lpa_server S, uint64_t ticket, int32_t* done, lpa_gra
     stats->iterations = r->iterations;
     stats->converged = r->converged;
     stats->edges_scanned = (int64_t)r->iterations * r->g.m;
+    stats->modularity = 0.0;
   }
   if (r->state == 2) {
     S->reqs.erase(it);

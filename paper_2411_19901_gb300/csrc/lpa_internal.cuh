@@ -209,11 +209,15 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
                                 const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
                                 int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
                                 cudaStream_t s);
-// Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.
+// Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.  With gid
+// (a batch), each graph's 2m and intra-community weight also accumulate into g2m / gin
+// (zeroed by the caller).
 cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const float* w,
                                    int64_t m, const int32_t* labels, int32_t n,
                                    const WarpPlan& p, double* sigma_c, double* partials,
-                                   int64_t npart, double* out4, cudaStream_t s);
+                                   int64_t npart, double* out4, cudaStream_t s,
+                                   const int32_t* gid = nullptr, double* g2m = nullptr,
+                                   double* gin = nullptr);
 int64_t modularity_plan_partials(const WarpPlan& p, int32_t n);
 
 cudaError_t launch_dn_sum(const unsigned long long* slots, unsigned long long* out,
@@ -260,6 +264,9 @@ cudaError_t launch_batch_converge(const BatchGraph* gs, int count, const uint32_
                                   DevState* st, int l, int pick_less, double tol, cudaStream_t s);
 cudaError_t launch_unpack_labels(const BatchGraph* gs, const int32_t* gid, const int32_t* c,
                                  int64_t nv, cudaStream_t s);
+// Per-graph Q after launch_modularity_plan with gid (lpa_modularity.cu).
+cudaError_t launch_batch_q(const BatchGraph* gs, int count, const double* sigma_c, const double* g2m,
+                           const double* gin, double* gq, cudaStream_t s);
 
 // Served form (lpa_batch.cu): per-graph stop test after a sweep, label carry-over into a
 // new packing (old_vb[g] < 0 for a new graph; gid and c_new point at vertex v0), output

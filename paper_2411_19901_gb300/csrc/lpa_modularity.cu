@@ -50,25 +50,44 @@ __device__ __forceinline__ double warp_down_sum(double x, int L, int Lw) {
   return x;
 }
 
+// Per-graph totals of a batch (gid null for a single graph): 2m_g and the intra-community
+// weight of graph g accumulate into g2m[g], gin[g].
+struct ModGraphs {
+  const int32_t* gid;
+  double* g2m;
+  double* gin;
+};
+
 // A block's vertex totals: Sigma_c through one atomic per distinct label among a warp's
-// owners, then the block's sums of K_i and of the intra-community weight into one of
-// kModSlots accumulators.  s_k, s_in: blockDim.x doubles of shared memory each.
-__device__ __forceinline__ void mod_commit(bool owner, int cv, double kv, double in,
+// owners, per-graph totals (batches) through one atomic per graph in a warp, then the
+// block's sums of K_i and of the intra-community weight into one of kModSlots
+// accumulators.  s_k, s_in: blockDim.x doubles of shared memory each.
+__device__ __forceinline__ void mod_commit(bool owner, int v, int cv, double kv, double in,
                                            double* sigma_c, double* slots, double* s_k,
-                                           double* s_in) {
+                                           double* s_in, const ModGraphs& mg) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const int key = owner ? cv : -(lane + 2);
-  const unsigned grp = __match_any_sync(kFullMask, key);
   s_k[tid] = owner ? kv : 0.0;
+  s_in[tid] = owner ? in : 0.0;
   __syncwarp();
+  const unsigned grp = __match_any_sync(kFullMask, owner ? cv : -(lane + 2));
   if (owner && lane == __ffs(grp) - 1) {
     double sum = 0.0;
     for (unsigned g = grp; g; g &= g - 1) sum += s_k[(tid & ~31) + __ffs(g) - 1];
     if (sum != 0.0) atomicAdd(sigma_c + cv, sum);
   }
-  __syncthreads();
-  s_k[tid] = owner ? kv : 0.0;
-  s_in[tid] = owner ? in : 0.0;
+  if (mg.gid != nullptr) {
+    const int gg = owner ? mg.gid[v] : -(lane + 2);
+    const unsigned same = __match_any_sync(kFullMask, gg);
+    if (owner && lane == __ffs(same) - 1) {
+      double a = 0.0, b = 0.0;
+      for (unsigned g = same; g; g &= g - 1) {
+        a += s_k[(tid & ~31) + __ffs(g) - 1];
+        b += s_in[(tid & ~31) + __ffs(g) - 1];
+      }
+      atomicAdd(mg.g2m + gg, a);
+      atomicAdd(mg.gin + gg, b);
+    }
+  }
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (tid < s) {
@@ -89,7 +108,7 @@ __device__ __forceinline__ void mod_commit(bool owner, int cv, double kv, double
 template <bool WT>
 __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
-    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots) {
+    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots, ModGraphs mg) {
   __shared__ double s_k[kLaneThreads], s_in[kLaneThreads];
   const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
   int v = -1, leaf = 0, L = 1;
@@ -113,14 +132,14 @@ __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
     kv = warp_down_sum(kv, L, Lw);
     in = warp_down_sum(in, L, Lw);
   }
-  mod_commit(v >= 0 && leaf == 0, acc.cv, kv, in, sigma_c, slots, s_k, s_in);
+  mod_commit(v >= 0 && leaf == 0, v, acc.cv, kv, in, sigma_c, slots, s_k, s_in, mg);
 }
 
 // Hubs of one class (p.hub_desc points at the class): the row split evenly over the CTA.
 template <bool WT>
 __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
-    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots) {
+    const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots, ModGraphs mg) {
   __shared__ double s_k[kThreads], s_in[kThreads];
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
@@ -143,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
   }
   const double kv = s_k[0], in = s_in[0];
   __syncthreads();
-  mod_commit(tid == 0, acc.cv, kv, in, sigma_c, slots, s_k, s_in);
+  mod_commit(tid == 0, v, acc.cv, kv, in, sigma_c, slots, s_k, s_in, mg);
 }
 
 __global__ void zero_f64_kernel(double* p, int64_t count) {
@@ -198,7 +217,37 @@ __global__ void __launch_bounds__(256) modularity_total_kernel(const double* slo
   }
 }
 
+// Batch: Q of graph g from its totals and the Sigma_c of its label range (one block per
+// graph; labels of graph g lie in [vb_g, vb_g + n_g)).
+__global__ void __launch_bounds__(256) batch_q_kernel(const BatchGraph* __restrict__ gs,
+                                                     const double* __restrict__ sigma_c,
+                                                     const double* __restrict__ g2m,
+                                                     const double* __restrict__ gin, double* gq) {
+  __shared__ double s[256];
+  const BatchGraph G = gs[blockIdx.x];
+  double acc = 0.0;
+  for (int64_t c = G.vb + threadIdx.x; c < G.vb + G.n; c += 256) acc += sigma_c[c] * sigma_c[c];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double two_m = g2m[blockIdx.x];
+    gq[blockIdx.x] = two_m > 0.0 ? gin[blockIdx.x] / two_m - s[0] / (two_m * two_m) : 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_q(const BatchGraph* gs, int count, const double* sigma_c, const double* g2m,
+                           const double* gin, double* gq, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  batch_q_kernel<<<count, 256, 0, s>>>(gs, sigma_c, g2m, gin, gq);
+  count_launch();
+  return cudaGetLastError();
+}
 
 int64_t modularity_plan_partials(const WarpPlan& p, int32_t n) {
   (void)p;
@@ -209,8 +258,10 @@ int64_t modularity_plan_partials(const WarpPlan& p, int32_t n) {
 cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const float* w,
                                    int64_t m, const int32_t* labels, int32_t n,
                                    const WarpPlan& p, double* sigma_c, double* partials,
-                                   int64_t npart, double* out4, cudaStream_t s) {
+                                   int64_t npart, double* out4, cudaStream_t s,
+                                   const int32_t* gid, double* g2m, double* gin) {
   (void)npart;
+  const ModGraphs mg{gid, g2m, gin};
   double* slots = partials;
   double* sq = partials + 2 * kModSlots;
   zero_f64_kernel<<<152 * 4, 256, 0, s>>>(sigma_c, n);
@@ -224,19 +275,19 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
     WarpPlan q = p;
     q.hub_desc = p.hub_desc + p.hub_start[c];
     if (w)
-      modularity_hub_kernel<true><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots);
+      modularity_hub_kernel<true><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
     else
-      modularity_hub_kernel<false><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots);
+      modularity_hub_kernel<false><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
     count_launch();
   }
   const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
   if (lane_ctas > 0) {
     if (w)
       modularity_lane_kernel<true><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
-                                                                               sigma_c, slots);
+                                                                               sigma_c, slots, mg);
     else
       modularity_lane_kernel<false><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
-                                                                                sigma_c, slots);
+                                                                                sigma_c, slots, mg);
     count_launch();
   }
   sigma_sq_kernel<<<kSqBlocks, 256, 0, s>>>(sigma_c, n, sq);

@@ -90,6 +90,7 @@ class lpa_graph_stats(ctypes.Structure):
         ("iterations", ctypes.c_int32),
         ("converged", ctypes.c_int32),
         ("edges_scanned", ctypes.c_int64),
+        ("modularity", ctypes.c_double),
     ]
 
 
@@ -391,7 +392,8 @@ def lpa_batch_detect(graphs, mode="mg", k=8, tol=0.05, max_iter=20,
                                    ctypes.cast(stats, ctypes.c_void_p),
                                    changed.ctypes.data))
     out = [{"iterations": int(stats[g].iterations), "converged": bool(stats[g].converged),
-            "edges_scanned": int(stats[g].edges_scanned)} for g in range(count)]
+            "edges_scanned": int(stats[g].edges_scanned),
+            "modularity": float(stats[g].modularity)} for g in range(count)]
     return out, changed[:count, :max_iter]
 
 

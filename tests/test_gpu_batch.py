@@ -112,3 +112,15 @@ def test_batch_validation_and_edge_cases(lpa):
         lpa.lpa_batch_detect(t[:1], mode="mg",
                              opt=lpa.make_options(labels_in=torch.zeros(good.n, dtype=torch.int32,
                                                                         device="cuda")))
+
+
+def test_batch_modularity_per_graph(lpa):
+    gs = batch_graphs()
+    labels, stats, _ = run_batch(lpa, gs, "mg", modularity=True)
+    for i, g in enumerate(gs):
+        ref = oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG, threads=4)
+        assert np.array_equal(labels[i], ref["labels"]), i
+        q = oracle.modularity(g.offsets, g.indices, g.weights, ref["labels"]) if g.n else 0.0
+        assert abs(stats[i]["modularity"] - q) <= 1e-9 * max(abs(q), 1e-3), (i, stats[i], q)
+    with pytest.raises(lpa.LpaError, match="sketch mode"):
+        run_batch(lpa, gs[:3], "exact", modularity=True)
