@@ -5,7 +5,9 @@
  * memory-efficient label choice of arxiv 2411.19901: a k-slot weighted Misra-Gries
  * sketch per vertex (Sec. 4.1-4.4, Alg. 1-2), the weighted Boyer-Moore variant
  * (Sec. 4.7, Alg. 3) and an exact per-vertex table mode (the ν-LPA baseline, Sec. 4,
- * Fig. 1), plus modularity (Sec. 3.2, Eq. 1).
+ * Fig. 1), plus modularity (Sec. 3.2, Eq. 1), pruning by unprocessed flags (Alg. 1),
+ * the paper-literal sketch and double scan (ablations), and batched and served forms
+ * for many graphs.
  *
  * Conventions for every entry point:
  *  - Graphs are CSR: offsets int64[n+1] (offsets[0] = 0, non-decreasing,
@@ -13,7 +15,9 @@
  *    NULL for unit weights.  The graph must be symmetric (w_ij = w_ji, Sec. 3); this is
  *    not checked.  Self-loops are allowed: the sweep skips them (the scan of Alg. 1
  *    skips j = i), modularity counts them once as stored.  Edges of weight 0 carry no
- *    vote.  n < 2^31, m < 2^62.
+ *    vote.  n < 2^31, m < 2^62.  indices and weights must start on a 16-byte boundary
+ *    (the sweep reads them as 16-byte vectors; cudaMalloc and PyTorch allocations do),
+ *    else LPA_EINVAL; lpa_graph entries of a batch or a server are exempt (copied).
  *  - Pointers are DEVICE memory owned by the caller unless marked "host".  The library
  *    frees nothing it did not allocate.
  *  - Calls are ordered on the caller's stream (lpa_options.stream; NULL = the legacy
