@@ -75,3 +75,45 @@ def test_full_size_sweeps_and_run(lpa, name):
     assert np.array_equal(got, ref["labels"]), np.nonzero(got != ref["labels"])[0][:10]
     q = oracle.modularity(g.offsets, g.indices, g.weights, ref["labels"])
     assert abs(st["modularity"] - q) <= 1e-9 * max(abs(q), 1e-3), (st["modularity"], q)
+
+
+def banded_graph(n, half):
+    """Vertex i joined to i +- 1 .. i +- half (mod n): every row has 2 * half entries, so
+    m = 2 * half * n; unit weights; symmetric."""
+    import synth
+
+    delta = np.concatenate([np.arange(-half, 0), np.arange(1, half + 1)]).astype(np.int64)
+    d = delta.size
+    idx = np.empty(n * d, dtype=np.int32)
+    step = 1 << 14
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        rows = np.arange(lo, hi, dtype=np.int64)[:, None]
+        idx[lo * d:hi * d] = ((rows + delta[None, :]) % n).astype(np.int32).ravel()
+    off = np.arange(n + 1, dtype=np.int64) * d
+    return synth.Graph(off, idx, None, f"banded_{n}_{half}")
+
+
+def test_more_than_2_31_entries(lpa):
+    """m = 2^31: CSR positions past the int32 range in every kernel (lane and hub
+    descriptors, the pipelined fold, the binning), compared sweep by sweep."""
+    g = banded_graph(1 << 20, 1024)
+    assert g.m == 1 << 31
+    dev = torch.device("cuda:0")
+    off = torch.from_numpy(g.offsets).to(dev)
+    idx = torch.from_numpy(g.indices).to(dev)
+    rng = np.random.default_rng(7)
+    c_prev = rng.integers(0, 1 << 12, g.n).astype(np.int32)  # few labels: hits and decrements
+    with lpa.Plan(off, idx, None, mode="mg", k=8, validate=True) as plan:
+        cp = torch.from_numpy(c_prev).to(dev)
+        cn = torch.empty_like(cp)
+        for pick_less in (True, False):
+            dn = plan.sweep(cp, cn, pick_less)
+            want, want_dn = oracle.move(g.offsets, g.indices, None, c_prev, mode=oracle.MG, k=8,
+                                        pick_less=pick_less, threads=THREADS)
+            got = cn.cpu().numpy()
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (pick_less, bad[:10], got[bad[:10]], want[bad[:10]])
+            assert dn == want_dn
+            c_prev = want
+            cp, cn = cn, cp
