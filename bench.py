@@ -42,8 +42,8 @@ UNIT = "edges/s"
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
 # hash of the sweep kernel source it was taken with.  If the source changes, traffic is
 # reported as null until a new capture is taken.
-SWEEP_TRAFFIC = {"src_sha256": "9c0ae3f771c958700c8671c9b7838da7570eb53cd3a737446284c9ff75e558dc", "workload": "lfr26",
-                 "bytes_per_launch": 37519733589}
+SWEEP_TRAFFIC = {"src_sha256": "c5549dde830ca87d7bd454ca4252934ca9e06b29a4417297fc850c5bbeff8d4d", "workload": "lfr26",
+                 "bytes_per_launch": 37525691989}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
