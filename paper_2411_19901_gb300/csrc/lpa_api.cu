@@ -948,9 +948,23 @@ lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
   const bool compact = P0.N > 0 && 2 * P0.dead_n > P0.N;
   if (!fresh.empty() || compact) {
     lpa_status rs = serve_admit(S, fresh, compact);
+    // on a failure before the fresh requests were placed, they go back to the queue
+    const bool placed =
+        fresh.empty() || std::find(S->slots.begin(), S->slots.end(), fresh.front()) != S->slots.end();
+    if (placed) {
+      S->used = used;
+      S->live += (int)fresh.size();
+    } else {
+      for (auto it = fresh.rbegin(); it != fresh.rend(); ++it) {
+        (*it)->state = 0;
+        S->waiting.push_front(*it);
+      }
+    }
     if (rs != LPA_OK) return rs;
-    S->used = used;
-    S->live += (int)fresh.size();
+  }
+  if (S->live > 0 && !S->pk.plan) {  // a previous re-plan failed: try again
+    lpa_status rs = replan(S);
+    if (rs != LPA_OK) return rs;
   }
   Packing& P = S->pk;
   if (S->live == 0 || !P.plan) {
