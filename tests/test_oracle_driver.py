@@ -188,3 +188,19 @@ def test_threads_do_not_change_results():
         b = oracle.lpa(g.offsets, g.indices, g.weights, mode=mode, threads=4, e0=2)
         assert np.array_equal(a["labels"], b["labels"])
         assert np.array_equal(a["changed"], b["changed"])
+
+
+def test_convergence_test_is_strict():
+    """Alg. 1 stops when dN / N < tau: a sweep with dN / N exactly tau does not stop.
+    Triangle 0-1-2 labelled (5, 5, 9) plus 17 isolated vertices (N = 20): only vertex 2
+    moves in the first sweep (to 5), so dN / N = 1 / 20, the same double as 0.05."""
+    g = synth.from_edges(20, [[0, 1], [1, 2], [0, 2]])
+    lab = np.arange(20, dtype=np.int32)
+    lab[:3] = [5, 5, 9]
+    assert 1.0 / 20.0 == 0.05
+    r = oracle.lpa(g.offsets, g.indices, None, mode=oracle.MG, rho=0, tol=0.05, labels_in=lab)
+    assert r["changed"].tolist() == [1, 0] and r["iterations"] == 2 and r["converged"]
+    above = float(np.nextafter(0.05, 1.0))
+    r = oracle.lpa(g.offsets, g.indices, None, mode=oracle.MG, rho=0, tol=above, labels_in=lab)
+    assert r["changed"].tolist() == [1] and r["iterations"] == 1 and r["converged"]
+    assert r["labels"][:3].tolist() == [5, 5, 5]
