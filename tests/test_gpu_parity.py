@@ -291,3 +291,18 @@ def test_memory_pool_release_and_reuse(lpa):
     h = np.empty(g.n, dtype=np.int32)
     lpa.lpa_detect_host(g.offsets, g.indices, g.weights, g.n, g.m, "mg", 8, 0.05, 20, h)
     assert np.array_equal(h, ref["labels"])
+
+
+def test_convergence_test_is_strict_on_the_device(lpa):
+    """dN / N exactly equal to tol does not stop the run (Alg. 1's strict test), on the
+    device as in the oracle: triangle (5, 5, 9) plus 17 isolated vertices, N = 20."""
+    g = synth.from_edges(20, [[0, 1], [1, 2], [0, 2]])
+    off, idx, w = to_dev(g)
+    lab = np.arange(20, dtype=np.int32)
+    lab[:3] = [5, 5, 9]
+    for tol in (0.05, float(np.nextafter(0.05, 1.0))):
+        labels, st = lpa.detect(off, idx, w, mode="mg", tol=tol, pl_period=0,
+                                labels_in=torch.from_numpy(lab).cuda())
+        ref = oracle.lpa(g.offsets, g.indices, None, mode=oracle.MG, rho=0, tol=tol, labels_in=lab)
+        assert st["changed"] == ref["changed"].tolist() and st["iterations"] == ref["iterations"]
+        assert np.array_equal(labels.cpu().numpy(), ref["labels"])
