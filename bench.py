@@ -69,15 +69,16 @@ WORKLOADS["serve"] = ("served form: Poisson arrivals at 2000 requests/s (seeded 
 SERVE_METRIC = "MG8-LPA served p99 latency"
 
 
-def make_graph(name: str) -> synth.Graph:
+def make_graph(name: str, threads: int | None = None) -> synth.Graph:
     if name == "lfr26":
         return synth.lfr(n=2**26, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
-                         cmax=10**6, mu=0.2, wmax=8, seed=0)
+                         cmax=10**6, mu=0.2, wmax=8, seed=0, threads=threads)
     if name == "lfr22":
         return synth.lfr(n=2**22, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
-                         cmax=10**6, mu=0.2, wmax=8, seed=0)
+                         cmax=10**6, mu=0.2, wmax=8, seed=0, threads=threads)
     if name == "rmat22":
-        return synth.rmat(scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=0)
+        return synth.rmat(scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=0,
+                          threads=threads)
     if name == "pp1000":
         return synth.planted_partition(n=1000, ncomm=10, p_in=0.1, p_out=0.005, seed=0)
     raise ValueError(name)
@@ -188,11 +189,27 @@ def physical_gpu_index(local_rank: int) -> int:
     return local_rank
 
 
-def share_graph(name: str, world: int, rank: int, barrier) -> tuple[synth.Graph, float]:
-    """Rank 0 generates; with several ranks the others map rank 0's arrays from disk."""
+# Approximate host bytes of each workload's CSR (offsets, indices, weights).
+GRAPH_BYTES = {"lfr26": 13 << 30, "rmat22": 2 << 30}
+
+
+def share_graph(name: str, world: int, rank: int, barrier,
+                need_bytes: int | None = None) -> tuple[synth.Graph, float]:
+    """Rank 0 generates; with several ranks the others map rank 0's arrays from disk.  If
+    the temporary directory lacks room for two copies of the graph, every rank generates
+    its own copy instead (same seed, same graph; the host cores split between ranks)."""
     t0 = time.perf_counter()
     if world == 1:
         g = make_graph(name)
+        return g, time.perf_counter() - t0
+    import shutil
+
+    need = GRAPH_BYTES.get(name, 1 << 30) if need_bytes is None else need_bytes
+    barrier()  # every rank looks at the directory before rank 0 writes to it
+    shared = shutil.disk_usage(tempfile.gettempdir()).free > 2 * need
+    barrier()
+    if not shared:
+        g = make_graph(name, threads=max(1, (os.cpu_count() or 1) // world))
         return g, time.perf_counter() - t0
     d = os.path.join(tempfile.gettempdir(), f"lpa_bench_{name}")
     if rank == 0:

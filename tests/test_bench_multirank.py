@@ -20,7 +20,7 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out_dir):
+def _rank_main(rank, world, port, out_dir, need_bytes=None):
     import sys
 
     sys.path.insert(0, ROOT)
@@ -31,7 +31,7 @@ def _rank_main(rank, world, port, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     w, r, loc = bench.dist_env()
     assert (w, r, loc) == (world, rank, rank)
-    g, _ = bench.share_graph("pp1000", world, rank, dist.barrier)
+    g, _ = bench.share_graph("pp1000", world, rank, dist.barrier, need_bytes=need_bytes)
     times, counts = bench.aggregate_over_ranks([1.0 + rank, 10.0 * (rank + 1)],
                                                [100.0, 7.0 + rank], world,
                                                torch.device("cpu"))
@@ -41,14 +41,16 @@ def _rank_main(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_share_the_graph_and_combine(tmp_path):
+@pytest.mark.parametrize("need_bytes", [None, 1 << 62])  # shared file / one copy per rank
+def test_two_gloo_ranks_share_the_graph_and_combine(tmp_path, need_bytes):
     import sys
 
     sys.path.insert(0, ROOT)
     import bench
 
     world = 2
-    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path), need_bytes), nprocs=world,
+             join=True)
     ref = bench.make_graph("pp1000")
     for rank in range(world):
         z = np.load(tmp_path / f"rank{rank}.npz")
