@@ -38,6 +38,20 @@ import synth  # noqa: E402
 METRIC = "MG8-LPA edges/sec/iteration"
 UNIT = "edges/s"
 
+
+def metric_name(args) -> str:
+    """The headline metric for MG with k = 8; the same quantity for another mode, k or
+    ablation variant is named after it."""
+    if args.mode == "mg":
+        name = f"MG{args.k}"
+        if args.unclamped:
+            name += "-literal"
+        if args.rescan:
+            name += "-rescan"
+    else:
+        name = {"bm": "BM", "exact": "exact"}[args.mode]
+    return f"{name}-LPA edges/sec/iteration"
+
 # DRAM traffic of one sweep (its hub and lane kernels together) measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
 # hash of the sweep kernel source it was taken with.  If the source changes, traffic is
@@ -193,11 +207,26 @@ def physical_gpu_index(local_rank: int) -> int:
 GRAPH_BYTES = {"lfr26": 13 << 30, "rmat22": 2 << 30}
 
 
+def _bcast_from_rank0(obj):
+    """rank 0's value of obj on every rank (torch.distributed must be initialised)."""
+    import torch.distributed as dist
+
+    box = [obj]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
 def share_graph(name: str, world: int, rank: int, barrier,
-                need_bytes: int | None = None) -> tuple[synth.Graph, float]:
-    """Rank 0 generates; with several ranks the others map rank 0's arrays from disk.  If
-    the temporary directory lacks room for two copies of the graph, every rank generates
-    its own copy instead (same seed, same graph; the host cores split between ranks)."""
+                need_bytes: int | None = None, free_bytes: int | None = None,
+                local_world: int | None = None, bcast=None) -> tuple[synth.Graph, float]:
+    """Rank 0 generates; with several ranks the others map rank 0's arrays from disk.
+
+    Rank 0 alone decides whether the graph is shared, and broadcasts the decision, so every
+    rank takes the same path: it is shared only when every rank runs on rank 0's node
+    (LOCAL_WORLD_SIZE == WORLD_SIZE, so all see rank 0's temporary directory) and that
+    directory has room for two copies of the graph.  Otherwise every rank generates its
+    own copy (same seed, same graph; the host cores split between ranks).  free_bytes and
+    local_world override what rank 0 reads from the system (tests)."""
     t0 = time.perf_counter()
     if world == 1:
         g = make_graph(name)
@@ -205,9 +234,11 @@ def share_graph(name: str, world: int, rank: int, barrier,
     import shutil
 
     need = GRAPH_BYTES.get(name, 1 << 30) if need_bytes is None else need_bytes
-    barrier()  # every rank looks at the directory before rank 0 writes to it
-    shared = shutil.disk_usage(tempfile.gettempdir()).free > 2 * need
-    barrier()
+    if local_world is None:
+        local_world = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+    if free_bytes is None:
+        free_bytes = shutil.disk_usage(tempfile.gettempdir()).free
+    shared = (bcast or _bcast_from_rank0)(bool(local_world == world and free_bytes > 2 * need))
     if not shared:
         g = make_graph(name, threads=max(1, (os.cpu_count() or 1) // world))
         return g, time.perf_counter() - t0
@@ -245,11 +276,13 @@ def aggregate_over_ranks(times_ms, counts, world: int, device):
 
 def sweep_bytes(n: int, m: int, weighted: bool) -> int:
     """Algorithmic bytes of one sweep: per CSR entry its index, weight and the gathered
-    neighbour label; per vertex its offset, old label and new label."""
-    return (12 if weighted else 8) * m + 16 * n
+    neighbour label (12 B, 8 B with unit weights); per vertex its offset, old label, new
+    label and its place in the degree order (8 + 4 + 4 + 4 = 20 B)."""
+    return (12 if weighted else 8) * m + 20 * n
 
 
-def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int):
+def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int, k: int = 8,
+                  unclamped: bool = False, rescan: bool = False):
     """Time full oracle sweeps (iteration 0 from identity labels) on all host cores."""
     import oracle
 
@@ -262,7 +295,8 @@ def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int):
     times = []
     while len(times) < max_reps and (not times or sum(times) < seconds):  # at least one
         t = time.perf_counter()
-        oracle.move(offs, idx, w, c0, mode=om, k=8, pick_less=True, threads=threads)
+        oracle.move(offs, idx, w, c0, mode=om, k=k, pick_less=True, threads=threads,
+                    unclamped=unclamped, rescan=rescan)
         times.append(time.perf_counter() - t)
     return times, threads
 
@@ -360,13 +394,14 @@ def run_reference(args):
 
     om_times, threads = [], 0
     for step in range(args.warmup + args.steps):
-        ts, threads = oracle_sweeps(g, args.mode, 0.0, 1)
+        ts, threads = oracle_sweeps(g, args.mode, 0.0, 1, k=args.k, unclamped=args.unclamped,
+                                    rescan=args.rescan)
         if step >= args.warmup:
             om_times += ts
     value = len(om_times) * g.m / sum(om_times)
     sample = f"{len(om_times)} full oracle sweeps (iteration 0 from identity labels) of the graph"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "impl": "reference", "metric": metric_name(args), "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(om_times) / len(om_times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -381,7 +416,8 @@ def run_reference(args):
 def config_of(args, g):
     return {
         "workload": f"{args.workload}: {WORKLOADS[args.workload]}",
-        "n": g.n, "m": g.m, "mode": args.mode, "k": 8, "tol": 0.05, "max_iter": 20,
+        "n": g.n, "m": g.m, "mode": args.mode, "k": args.k, "tol": 0.05, "max_iter": 20,
+        "mg_variant": {"unclamped": args.unclamped, "rescan": args.rescan},
         "pl_period": 8, "weights": "int-valued fp32" if g.weights is not None else "unit",
         "l2": "inputs larger than L2 (no flush)" if g.m * 8 > 129e6 else
               "inputs smaller than L2 (warm cache)",
@@ -425,14 +461,15 @@ def run_ours(args):
     d_idx = h_idx.to(dev)
     d_w = h_w.to(dev) if weighted else None
     labels = torch.empty(n, dtype=torch.int32, device=dev)
-    ws = torch.empty(lpa.lpa_workspace_size(n, m, args.mode), dtype=torch.uint8, device=dev)
+    ws = torch.empty(lpa.lpa_workspace_size(n, m, args.mode, args.k), dtype=torch.uint8,
+                     device=dev)
     stream = torch.cuda.current_stream(dev)
     opt = lpa.make_options(validate=False, timing=True, modularity=True, stream=stream,
-                           workspace=ws)
+                           workspace=ws, unclamped=args.unclamped, rescan=args.rescan)
 
     def step():
         st = lpa.lpa_stats()
-        lpa.lpa_detect_ex(d_off, d_idx, d_w, n, m, args.mode, 8, 0.05, 20, labels, st, opt)
+        lpa.lpa_detect_ex(d_off, d_idx, d_w, n, m, args.mode, args.k, 0.05, 20, labels, st, opt)
         return st.to_dict()
 
     for _ in range(args.warmup):
@@ -469,9 +506,10 @@ def run_ours(args):
     def e2e_call():
         st = lpa.lpa_stats()
         lpa.lpa_detect_host(h_off.numpy(), h_idx.numpy(), h_w.numpy() if weighted else None,
-                            n, m, args.mode, 8, 0.05, 20, h_lab.numpy(), st,
+                            n, m, args.mode, args.k, 0.05, 20, h_lab.numpy(), st,
                             lpa.make_options(validate=False, modularity=True, stream=stream,
-                                             workspace=ws))
+                                             workspace=ws, unclamped=args.unclamped,
+                                             rescan=args.rescan))
         return st.to_dict()
 
     e2e_call()
@@ -489,6 +527,19 @@ def run_ours(args):
     barrier()
     e2e_edges = sum(s["iterations"] * m for s in e2e_stats)
 
+    # the standalone modularity entry point (Eq. 1) on the final labels, outside the timed
+    # region: CUDA events around lpa_modularity_ex calls, after one untimed call
+    mopt = lpa.make_options(validate=False, stream=stream)
+    lpa.lpa_modularity_ex(d_off, d_idx, d_w, n, m, labels, mopt)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(3):
+        q_alone = lpa.lpa_modularity_ex(d_off, d_idx, d_w, n, m, labels, mopt)
+    m1.record(stream)
+    torch.cuda.synchronize(dev)
+    mod_ms = m0.elapsed_time(m1) / 3
+    mod_bytes = (12 if weighted else 8) * m + 16 * n
+
     (elapsed_ms, e2e_ms), (edges_all, e2e_edges_all) = aggregate_over_ranks(
         [elapsed_ms, e2e_ms], [edges, e2e_edges], world, dev)
 
@@ -501,14 +552,15 @@ def run_ours(args):
 
     peak, peak_kind = measured_hbm_peak()
     launch_ms = sweep_ms / max(sweeps, 1)
-    alg_bytes = sweep_bytes(n, m, weighted)
+    alg_bytes = sweep_bytes(n, m, weighted) + (sweep_bytes(0, m, weighted) if args.rescan else 0)
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     traffic = None
     if SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha() and SWEEP_TRAFFIC["workload"] == args.workload:
         traffic = SWEEP_TRAFFIC["bytes_per_launch"]
     cpu = None
     if world == 1:
-        times, threads = oracle_sweeps(g, args.mode, seconds=10.0, max_reps=3)
+        times, threads = oracle_sweeps(g, args.mode, seconds=10.0, max_reps=3, k=args.k,
+                                       unclamped=args.unclamped, rescan=args.rescan)
         cpu = {"value": len(times) * m / sum(times), "unit": UNIT, "cores": threads,
                "kind": "oracle",
                "sample": f"{len(times)} full oracle sweep(s) (iteration 0 from identity "
@@ -516,7 +568,7 @@ def run_ours(args):
     h2d = 8 * (n + 1) + 4 * m + (4 * m if weighted else 0)
     d2h = 4 * n + 64 + 32 + 64 + 8 * 20
     line = {
-        "metric": METRIC, "value": edges_all / (elapsed_ms * 1e-3), "unit": UNIT,
+        "metric": metric_name(args), "value": edges_all / (elapsed_ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -539,6 +591,9 @@ def run_ours(args):
         "iterations": [s["iterations"] for s in stats],
         "sweep_ms_iter": [round(x, 3) for x in stats[-1]["sweep_ms_iter"]],
         "modularity": stats[-1]["modularity"],
+        "modularity_standalone": {"ms": mod_ms, "q": q_alone, "algorithmic_bytes": mod_bytes,
+                                  "achieved_gbs": mod_bytes / (mod_ms * 1e-3) / 1e9,
+                                  "call": "lpa_modularity_ex (no plan), mean of 3"},
         "setup_ms": stats[-1]["setup_ms"],
         "generate_s": gen_s,
     }
@@ -754,6 +809,7 @@ def run_serve(args):
     steps = 0
     step_time = 0.0
     inflight_sum = 0
+    step_admit, step_plain = [], []  # host ms of steps that admitted requests / did not
     torch.cuda.synchronize(dev)
     start = time.perf_counter()
     clocks.mark("start")
@@ -762,6 +818,7 @@ def run_serve(args):
         if not inflight and nxt < total and arrive[nxt] > now:
             time.sleep(max(0.0, arrive[nxt] - now))
             now = time.perf_counter() - start
+        admitted = False
         while nxt < total and arrive[nxt] <= now:
             ho, hi, hw = host[pick[nxt]]
             do = ho.to(dev, non_blocking=True)
@@ -770,11 +827,14 @@ def run_serve(args):
             out = torch.empty(do.numel() - 1, dtype=torch.int32, device=dev)
             inflight[srv.submit(do, di, dw, out)] = (nxt, out)
             nxt += 1
+            admitted = True
         t_step = time.perf_counter()
         srv.step()
         steps += 1
         t_done = time.perf_counter() - start
-        step_time += time.perf_counter() - t_step
+        dt_step = time.perf_counter() - t_step
+        step_time += dt_step
+        (step_admit if admitted else step_plain).append(1e3 * dt_step)
         inflight_sum += len(inflight)
         for tk in srv.drain():
             st = srv.poll(tk)
@@ -797,9 +857,17 @@ def run_serve(args):
         solo, _ = lpa.detect(ho.to(dev), hi.to(dev), None if hw is None else hw.to(dev),
                              mode=args.mode, validate=False)
         equal = equal and bool(torch.equal(solo, out))
+    one = serve_one_at_a_time(lpa, host, gpool, arrive, pick, n_warm, args, stream)
     if rank != 0:
         return
     entries = np.array([gpool[j].m for j in pick])
+    kind = np.where(pick[n_warm:] >= 512, "rmat20", "sbm")
+
+    def pct(x, q):
+        return float(np.percentile(x, q)) if len(x) else None
+
+    def mean(x):
+        return float(np.mean(x)) if len(x) else None
     cpu = None
     if world == 1:
         olat, threads = oracle_serve_latencies(gpool, args.mode, 10.0)
@@ -821,7 +889,14 @@ def run_serve(args):
         "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
         "throughput_per_s": float(n_timed / span),
         "edge_visits_per_s": float((iters[n_warm:] * entries[n_warm:]).sum() / span),
+        "by_kind": {k: {"requests": int((kind == k).sum()), "p50_ms": pct(lat[kind == k], 50),
+                        "p99_ms": pct(lat[kind == k], 99)} for k in ("sbm", "rmat20")},
+        "one_at_a_time": one,
         "server_steps": steps, "step_ms_mean": 1e3 * step_time / max(steps, 1),
+        "step_ms": {"admitting": {"steps": len(step_admit), "mean": mean(step_admit),
+                                  "p99": pct(step_admit, 99)},
+                    "sweep_only": {"steps": len(step_plain), "mean": mean(step_plain),
+                                   "p99": pct(step_plain, 99)}},
         "in_flight_mean": inflight_sum / max(steps, 1),
         "bit_equal_sampled": equal, "sampled": len(outputs),
         "roofline": None, "cpu_baseline": cpu,
@@ -835,6 +910,34 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_one_at_a_time(lpa, host, gpool, arrive, pick, n_warm, args, stream):
+    """The same arrival stream served first come, first served by one lpa_detect_host call
+    per request on the same GPU (graph copied in from page-locked memory, labels copied
+    back); latency = completion - arrival, over the requests after the warm-up ones."""
+    import torch
+
+    total = len(arrive)
+    opt = lpa.make_options(validate=False, stream=stream)
+    out = torch.empty(max(g.n for g in gpool), dtype=torch.int32, pin_memory=True)
+    done_at = np.zeros(total)
+    start = time.perf_counter()
+    for i in range(total):
+        now = time.perf_counter() - start
+        if arrive[i] > now:
+            time.sleep(arrive[i] - now)
+        ho, hi, hw = host[pick[i]]
+        g = gpool[pick[i]]
+        lpa.lpa_detect_host(ho.numpy(), hi.numpy(), None if hw is None else hw.numpy(), g.n,
+                            g.m, args.mode, 8, 0.05, 20, out.numpy(), None, opt)
+        done_at[i] = time.perf_counter() - start
+    lat = (done_at - arrive)[n_warm:] * 1e3
+    span = done_at[n_warm:].max() - arrive[n_warm]
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "throughput_per_s": float((total - n_warm) / span),
+            "how": "FIFO, one lpa_detect_host per request (host graph in, labels out)"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -843,7 +946,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lfr26")
     ap.add_argument("--mode", choices=["mg", "bm", "exact"], default="mg")
+    ap.add_argument("--k", type=int, choices=[1, 2, 4, 8, 16, 32], default=8,
+                    help="MG sketch slots (single-graph workloads)")
+    ap.add_argument("--unclamped", action="store_true",
+                    help="MG ablation: the accumulate exactly as printed (LPA_MG_UNCLAMPED)")
+    ap.add_argument("--rescan", action="store_true",
+                    help="MG ablation: the double scan of Sec. 4.4 (LPA_RESCAN)")
     args = ap.parse_args()
+    if args.mode != "mg" and (args.k != 8 or args.unclamped or args.rescan):
+        ap.error("--k, --unclamped and --rescan apply to --mode mg")
     if args.warmup < 3:
         print("note: the timing rules want at least 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

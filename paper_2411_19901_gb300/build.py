@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblpa.so")
 SOURCES = ["lpa_api.cu", "lpa_sweep.cu", "lpa_sweep_k16.cu", "lpa_sweep_k32.cu",
-           "lpa_sweep_variants.cu", "lpa_exact.cu", "lpa_modularity.cu", "lpa_setup.cu", "lpa_batch.cu",
+           "lpa_sweep_variants.cu", "lpa_sweep_variants_k16.cu", "lpa_sweep_variants_k32.cu",
+           "lpa_exact.cu", "lpa_modularity.cu", "lpa_setup.cu", "lpa_batch.cu",
            "lpa_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -105,6 +105,13 @@ int64_t hub_cap(int64_t n, int64_t m, int e0) {
 int64_t lane_cap(int64_t n, int64_t m, int e0) {
   return n + std::min<int64_t>(m / e0, 31 * n) + 32 * num_windows(n);
 }
+// Elements (groups of four positions) of the sliced copy: a lane leaf of len positions
+// takes ceil(len / 4) <= len / 4 + 3/4, a hub of d positions and L leaves L * G with
+// G <= (d / L + 4) / 4, so L * G <= d / 4 + L; L <= 256, and L <= d / e0 once L > 1.
+int64_t slice_cap(int64_t n, int64_t m, int e0) {
+  const int64_t hubs = hub_cap(n, m, e0);
+  return m / 4 + 1 + lane_cap(n, m, e0) + std::min<int64_t>(256 * hubs, m / e0 + hubs);
+}
 
 // Workspace layout of a plan; offsets in bytes from the workspace base.
 struct Layout {
@@ -112,7 +119,8 @@ struct Layout {
   size_t act, scanned, scan_total;  // pruning: two flag arrays, per-iteration counters
   // sketch modes
   size_t desc, wtab, hcnt, lcnt, hub_prefix, lane_prefix, hub_desc, lane_desc, counts;
-  int64_t hub_cap, lane_cap;
+  size_t sl_cnt, sl_base, sl_idx, sl_w;  // the sliced copy of the CSR and its bases
+  int64_t hub_cap, lane_cap, sl_cap;
   // exact mode
   size_t cv0, cv1, hubs, hub_tab, seg;
   // modularity
@@ -120,7 +128,7 @@ struct Layout {
   size_t total_fixed, tab_keys, tab_vals, total;
 };
 
-Layout layout(int64_t n, int64_t m, int mode, int e0, int64_t tab_slots) {
+Layout layout(int64_t n, int64_t m, int mode, int e0, bool weighted, int64_t tab_slots) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -155,6 +163,12 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int64_t tab_slots) {
     L.hub_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.hub_cap, 1));
     L.lane_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.lane_cap, 1));
     L.counts = take(sizeof(unsigned long long) * 8);
+    L.sl_cap = slice_cap(n, m, e0);
+    const int64_t nbase = L.lane_cap / 32 + L.hub_cap + 1;
+    L.sl_cnt = take(sizeof(int32_t) * (size_t)nbase);
+    L.sl_base = take(sizeof(int64_t) * (size_t)nbase);
+    L.sl_idx = take(sizeof(int4) * (size_t)L.sl_cap);
+    L.sl_w = weighted ? take(sizeof(float4) * (size_t)L.sl_cap) : 0;
     WarpPlan dummy{};
     L.partials = take(sizeof(double) * (size_t)modularity_plan_partials(dummy, (int32_t)n));
   }
@@ -347,8 +361,26 @@ lpa_status bin_classes(lpa_plan_s* p) {
   for (int c = 0; c <= kHubClasses; ++c) wp.hub_start[c] = (int32_t)p->host_cls[8 + c];
   wp.nlanes = nlanes;
   wp.nctas = (int32_t)nctas;
+  wp.e0 = p->e0;
+  wp.lmax = p->lmax;
   p->nhubs = nhubs;
   p->nchunks = nctas - nhubs;
+  // the sliced copy of the CSR that the sweeps read
+  int64_t* base = (int64_t*)(p->ws + ly.sl_base);
+  wp.lane_base = base;
+  wp.hub_base = base + nlanes / 32;
+  LPA_CUDA(launch_slice_count(wp, p->e0, p->lmax, (int32_t*)(p->ws + ly.sl_cnt), base, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 16, base + nlanes / 32 + nhubs, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaStreamSynchronize(s));
+  const int64_t groups = (int64_t)p->host_cls[16];
+  if (groups < 0 || groups > ly.sl_cap)
+    return fail(LPA_EINTERNAL, "sliced copy of %lld groups exceeds its bound %lld",
+                (long long)groups, (long long)ly.sl_cap);
+  wp.sl_idx = (const int4*)(p->ws + ly.sl_idx);
+  wp.sl_w = p->w ? (const float4*)(p->ws + ly.sl_w) : nullptr;
+  LPA_CUDA(launch_slice_fill(p->idx, p->w, wp, p->e0, p->lmax, (int4*)wp.sl_idx,
+                             (float4*)wp.sl_w, s));
   return LPA_OK;
 }
 
@@ -451,7 +483,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
 
   // workspace: fixed part now; exact-mode hub tables once binning knows their size
-  p->lay = layout(n, m, p->mode, p->e0, p->mode == kExact ? 2 * m : 0);
+  p->lay = layout(n, m, p->mode, p->e0, weights != nullptr, p->mode == kExact ? 2 * m : 0);
   if (o.workspace) {
     if (o.workspace_bytes < p->lay.total)
       return bail(fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, p->lay.total));
@@ -527,7 +559,7 @@ cudaError_t launch_plan_modularity(const lpa_plan_s* p, const int32_t* labels) {
   double* partials = (double*)(p->ws + p->lay.partials);
   double* out4 = (double*)(p->ws + p->lay.out4);
   if (p->mode == kExact)
-    return launch_modularity(p->off, p->idx, p->w, labels, p->n, sigma, partials,
+    return launch_modularity(p->off, p->idx, p->w, p->m, labels, p->n, sigma, partials,
                              modularity_partials(p->n), out4, p->stream);
   return launch_modularity_plan(p->off, p->idx, p->w, p->m, labels, p->n, p->wp, sigma, partials,
                                 modularity_plan_partials(p->wp, p->n), out4, p->stream);
@@ -726,10 +758,14 @@ struct Packing {
 };
 
 // HBM a resident graph takes: packed CSR (8 B offset + 4 B index (+ 4 B weight) per entry),
-// graph id and two labels per vertex, and the plan's vertex and lane descriptors.
+// graph id and two labels per vertex, the plan's vertex and lane descriptors, and its
+// sliced copy of the indices (and weights): 16 B per group of four, about one group per
+// leaf more than the entries fill.
 size_t serve_footprint(const lpa_graph& g, int e0) {
   const size_t n = (size_t)g.n, m = (size_t)g.m;
-  return 8 * (n + 1) + 8 * m + 12 * n + 32 * n + 16 * (m / (size_t)e0 + 32) + 1024;
+  const size_t lanes = n + m / (size_t)e0 + 32;
+  return 8 * (n + 1) + 8 * m + 12 * n + 32 * n + 16 * lanes +
+         (g.weights ? 2 : 1) * 16 * (m / 4 + lanes) + 1024;
 }
 
 }  // namespace
@@ -1024,6 +1060,15 @@ lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
 
 }  // namespace
 
+int lpa::check_modularity_args(const int64_t* offsets, const int32_t* indices, int32_t n,
+                               int64_t m, const int32_t* labels, const double* q_out) {
+  lpa_status s = check_graph_args(offsets, indices, n, m);
+  if (s != LPA_OK) return s;
+  if (!q_out) return fail(LPA_EINVAL, "q_out is NULL");
+  if (n > 0 && !labels) return fail(LPA_EINVAL, "labels is NULL");
+  return LPA_OK;
+}
+
 extern "C" {
 
 void lpa_options_init(lpa_options* opt) {
@@ -1045,7 +1090,7 @@ size_t lpa_workspace_size_ex(int32_t n, int64_t m, lpa_mode mode, int32_t k,
   if (n < 0 || m < 0) return 0;
   const int e0 = opt ? opt->leaf_e0 : 64;
   if (e0 < 1) return 0;
-  return layout(n, m, (int)mode, e0, mode == LPA_EXACT ? 2 * m : 0).total;
+  return layout(n, m, (int)mode, e0, true, mode == LPA_EXACT ? 2 * m : 0).total;
 }
 
 size_t lpa_modularity_workspace_size(int32_t n) {
@@ -1169,10 +1214,8 @@ lpa_status lpa_detect_host(const int64_t* offsets, const int32_t* indices, const
 lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices, const float* weights,
                              int32_t n, int64_t m, const int32_t* labels, double* q_out,
                              const lpa_options* opt) {
-  lpa_status s = check_graph_args(offsets, indices, n, m);
+  lpa_status s = (lpa_status)check_modularity_args(offsets, indices, n, m, labels, q_out);
   if (s != LPA_OK) return s;
-  if (!q_out) return fail(LPA_EINVAL, "q_out is NULL");
-  if (n > 0 && !labels) return fail(LPA_EINVAL, "labels is NULL");
   lpa_options o;
   lpa_options_init(&o);
   if (opt) o = *opt;
@@ -1206,7 +1249,7 @@ lpa_status lpa_modularity_ex(const int64_t* offsets, const int32_t* indices, con
       return fail(LPA_EINVAL, "invalid input (error bits 0x%x)", host_st.err);
     }
   }
-  if (ce == cudaSuccess) ce = launch_modularity(offsets, indices, weights, labels, n, sigma_c, partials, npart, out3, st);
+  if (ce == cudaSuccess) ce = launch_modularity(offsets, indices, weights, m, labels, n, sigma_c, partials, npart, out3, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_out, out3, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
   if (own) cudaFreeAsync(ws, st);
   cudaError_t ce2 = cudaStreamSynchronize(st);

@@ -412,4 +412,81 @@ __device__ __forceinline__ void fold_range(S& st, const int32_t* __restrict__ id
 #undef LPA_STEP
 }
 
+// ---------------------------------------------------------------- sliced fold
+
+// Where a lane's groups sit in its warp's slice (see WarpPlan): column k holds group k of
+// every lane that has one, in lane order.  at(k) takes a warp vote, so every lane of the
+// warp calls it for k = 0, 1, 2, ... in turn.
+struct LaneSliceAddr {
+  int64_t col;      // first element of the next column
+  int groups;       // this lane's groups in the slice
+  unsigned below;   // mask of the lanes below this one
+  __device__ __forceinline__ int64_t at(int k) {
+    const unsigned has = __ballot_sync(kFullMask, groups > k);
+    const int64_t p = col + __popc(has & below);
+    col += __popc(has);
+    return p;
+  }
+};
+
+// Where a hub leaf's groups sit: a fixed stride from its first one.
+struct HubSliceAddr {
+  int64_t first;
+  int stride;
+  __device__ __forceinline__ int64_t at(int k) const { return first + (int64_t)k * stride; }
+};
+
+// Fold the len positions of one leaf, in CSR order, from the sliced copy into st, with
+// the same rule as fold_range: st.add(C[j], w) for every kept position.  The leaf has ng
+// groups (0: nothing to fold); the loop takes `iters` >= ng steps, the same on every lane
+// when addr votes, and steps past ng only keep the vote going.  Same three-set pipeline
+// as fold_range: while group k is folded, the labels of group k+1 are gathered and group
+// k+2 is loaded; the loads of a warp's lanes are side by side in memory.
+template <class S, bool WT, bool SKIP_SELF, class A>
+__device__ __forceinline__ void fold_groups(S& st, const int4* __restrict__ si,
+                                            const float4* __restrict__ sw,
+                                            const int32_t* __restrict__ lab, int self, int len,
+                                            int ng, int iters, A& addr) {
+  if (iters <= 0) return;
+  const unsigned lastm = 0xFu >> ((4 - (len & 3)) & 3);  // positions of the last group
+  auto load = [&](int k, int4& X, float4& W) {
+    const int64_t p = addr.at(k);
+    if (k < ng) {
+      X = __ldg(si + p);
+      W = WT ? __ldg(sw + p) : make_float4(1.f, 1.f, 1.f, 1.f);
+    } else {
+      X = make_int4(self, self, self, self);
+      W = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto gather = [&](int k, int4& X, const float4& W) {
+    const unsigned mk = k < ng ? (k == ng - 1 ? lastm : 0xFu) : 0u;
+    X = gather_group<SKIP_SELF>(lab, X, W, mk, self);
+  };
+  auto fold = [&](int4 C, float4 W) {
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+      if (C.x >= 0) st.add(C.x, W.x);
+      C = make_int4(C.y, C.z, C.w, -1);
+      W = make_float4(W.y, W.z, W.w, 0.f);
+    }
+  };
+  int4 X0, X1 = make_int4(self, self, self, self), X2 = make_int4(self, self, self, self);
+  float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  load(0, X0, W0);
+  gather(0, X0, W0);
+  if (iters > 1) load(1, X1, W1);
+#define LPA_STEP(XF, WF, XG, WG, XL, WL)   \
+  if (k + 1 < iters) gather(k + 1, XG, WG); \
+  if (k + 2 < iters) load(k + 2, XL, WL);   \
+  fold(XF, WF);                             \
+  if (++k >= iters) break;
+  for (int k = 0;;) {
+    LPA_STEP(X0, W0, X1, W1, X2, W2)
+    LPA_STEP(X1, W1, X2, W2, X0, W0)
+    LPA_STEP(X2, W2, X0, W0, X1, W1)
+  }
+#undef LPA_STEP
+}
+
 }  // namespace lpa

@@ -96,15 +96,34 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
   return (int)(p < lmax ? p : lmax);
 }
 
-// Binned graph as the warp-per-row kernels see it.
+// Sliced copy of the CSR (built once per plan).  A leaf's positions, in CSR order, are
+// cut into ceil(len / 4) groups of four (the last one padded with {self, weight 0}); each
+// group is one 16-byte element of sl_idx and of sl_w, so the lanes of a warp read their
+// groups side by side instead of 32 separate rows.
+//  * lane warps: column k of a warp holds group k of every lane that has one, in lane
+//    order (a warp vote gives each lane its place), so a warp's slice has exactly the
+//    groups of its lanes; lane_base[w] is its first element.
+//  * hubs of L leaves: width W = min(32, L); group k of leaf t sits at
+//    hub_base[h] + (t / 32) * W * G + k * W + t % 32, with G = ceil(ceil(d / L) / 4) the
+//    groups of the longest leaf.
 struct WarpPlan {
   const int4* hub_desc;   // per hub: {v, offset lo, offset hi, degree}, grouped by class
   const int4* lane_desc;  // per lane (see kLaneLeafShift); v = -1 on padding lanes
+  const int4* sl_idx;     // sliced copy of the indices
+  const float4* sl_w;     // sliced copy of the weights (null: unit weights)
+  const int64_t* lane_base;  // first sliced element of each lane warp
+  const int64_t* hub_base;   // first sliced element of each hub (in hub_desc order)
   int64_t nlanes;         // a multiple of 32
   int32_t nhubs;
   int32_t nctas;          // nhubs + ceil(nlanes / kThreads) (work units, for the stats)
+  int32_t e0, lmax;       // the leaf partition the plan was binned with
   int32_t hub_start[kHubClasses + 1];  // first hub of each class; [kHubClasses] = nhubs
 };
+
+// Groups of four positions a hub leaf is padded to (the longest of its L leaves).
+__host__ __device__ __forceinline__ int64_t hub_leaf_groups(int64_t d, int L) {
+  return ((d + L - 1) / L + 3) / 4;
+}
 
 // Arguments of one sweep launch.
 struct SweepArgs {
@@ -189,6 +208,10 @@ cudaError_t launch_sweep_mg32(bool weighted, const SweepArgs& a, const WarpPlan&
 cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, bool weighted,
                                     const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
                                     cudaStream_t s_hub);
+cudaError_t launch_sweep_mg16_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+                                      const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
+cudaError_t launch_sweep_mg32_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+                                      const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
 // Weight profile: out[0] = 1 if every weight is integer-valued (AND), out[1] = largest
 // weight's bits, out[2] = largest row length.  out must be zeroed except out[0] = 1.
 cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n, int64_t m,
@@ -209,6 +232,15 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
                                 const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
                                 int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
                                 cudaStream_t s);
+// Sliced copy of the CSR for a binned plan (lpa_setup.cu).  cnt: nlanes / 32 + nhubs
+// int32 scratch; base: their exclusive prefix (nlanes / 32 + nhubs + 1 int64), so
+// base[nlanes / 32 + h] is hub h's first element and base[end] the total.  Pass 1 counts
+// and scans; pass 2 (after the host has checked the total against the capacity) fills
+// sl_idx / sl_w (sl_w null for unit weights).
+cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
+                               cudaStream_t s);
+cudaError_t launch_slice_fill(const int32_t* idx, const float* w, const WarpPlan& p, int e0,
+                              int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s);
 // Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.  With gid
 // (a batch), each graph's 2m and intra-community weight also accumulate into g2m / gin
 // (zeroed by the caller).
@@ -240,11 +272,12 @@ cudaError_t launch_finalize(const DevState* st, int32_t* out, const int32_t* tmp
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, int64_t count, cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long value, int64_t count,
                             cudaStream_t s);
-// Modularity: out4 receives {2m, sum of intra-community weight, sum_c Sigma_c^2, Q}.
-cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const float* w,
+// Modularity without a plan (lpa_modularity.cu): out4 receives {2m, sum of
+// intra-community weight, sum_c Sigma_c^2, Q}.  sigma_c: n doubles; partials: 3 * npart
+// doubles with npart = modularity_partials(n).  Neither needs clearing.
+cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const float* w, int64_t m,
                               const int32_t* labels, int32_t n, double* sigma_c,
-                              double* partials, int32_t npart, double* out3,
-                              cudaStream_t s);
+                              double* partials, int32_t npart, double* out4, cudaStream_t s);
 int modularity_partials(int32_t n);
 
 inline int64_t num_segments(int64_t n) { return (n + kSegment - 1) / kSegment; }
@@ -283,6 +316,10 @@ cudaError_t launch_unpack_finished(const BatchGraph* gs, const int32_t* gid, con
 
 // Record the message returned by lpa_last_error() on this host thread; returns s.
 int set_last_error(int s, const char* msg);
+// Argument checks shared by the modularity entry points (a status of lpa.h; the message
+// is recorded as by set_last_error).
+int check_modularity_args(const int64_t* offsets, const int32_t* indices, int32_t n, int64_t m,
+                          const int32_t* labels, const double* q_out);
 
 // Kernels launched by the library (counted at every launch site).
 extern std::atomic<unsigned long long> g_launches;

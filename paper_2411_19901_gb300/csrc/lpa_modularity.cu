@@ -1,11 +1,12 @@
-// lpa_modularity.cu -- modularity (Sec. 3.2, Eq. 1) over the binned graph of a run:
+// lpa_modularity.cu -- modularity (Sec. 3.2, Eq. 1):
 // Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2, accumulated in fp64.
 //
-// The rows pass reuses the sweep's work map (hub kernels per CTA-size class, packed lane
-// descriptors) and its pipelined row reads, so it streams the CSR at the sweep's rate.
-// Per vertex it forms K_i (all entries, self-loops included, as stored) and the weight of
-// entries whose neighbour shares the label; Sigma_c receives K_i through one atomic per
-// run of equal labels in a warp.  Block sums go to kModSlots accumulators.
+// Two rows passes.  The one of a run reuses the sweep's work map (hub kernels per
+// CTA-size class, packed lane descriptors) and its pipelined row reads, so it streams
+// the CSR at the sweep's rate.  The standalone one (lpa_modularity*, no plan) needs no
+// work map: a warp takes 32 consecutive vertices.  Per vertex both form K_i (all
+// entries, self-loops included, as stored) and the weight of entries whose neighbour
+// shares the label; Sigma_c receives K_i through one atomic per distinct label in a warp.
 #include "lpa_fold.cuh"
 
 namespace lpa {
@@ -122,10 +123,11 @@ __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
     L = 1 << (l.w >> kLaneLgShift);
   }
   ModAcc acc{0.f, 0.f, 0.f, 0.f, -1};
-  if (v >= 0) {
-    acc.cv = labels[v];
-    fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, lo, lo + len);
-  }
+  if (v >= 0) acc.cv = labels[v];
+  const int ngl = (int)((len + 3) >> 2);
+  LaneSliceAddr ad{q < p.nlanes ? p.lane_base[q >> 5] : 0, ngl, (1u << (threadIdx.x & 31)) - 1u};
+  fold_groups<ModAcc, WT, false>(acc, p.sl_idx, p.sl_w, labels, v, (int)len, ngl,
+                                 __reduce_max_sync(kFullMask, ngl), ad);
   double kv = acc.k(), in = acc.in();
   const int Lw = __reduce_max_sync(kFullMask, L);
   if (Lw > 1) {
@@ -135,7 +137,8 @@ __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
   mod_commit(v >= 0 && leaf == 0, v, acc.cv, kv, in, sigma_c, slots, s_k, s_in, mg);
 }
 
-// Hubs of one class (p.hub_desc points at the class): the row split evenly over the CTA.
+// Hubs of one class (p.hub_desc, p.hub_base point at the class): leaf t on thread t, from
+// the sliced copy.
 template <bool WT>
 __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
@@ -147,9 +150,16 @@ __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
   const int v = h.x;
   const int64_t base = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
   const int64_t d = h.w;
+  const int L = leaf_count(d, p.e0, p.lmax);
   ModAcc acc{0.f, 0.f, 0.f, 0.f, labels[v]};
-  fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, base + (tid * d) / nt,
-                                base + ((tid + 1) * d) / nt);
+  if (tid < L) {  // leaf tid from the sliced copy
+    const int64_t lo = base + (tid * d) / L, len = base + ((tid + 1) * d) / L - lo;
+    const int W = L < 32 ? L : 32;
+    const int64_t G = hub_leaf_groups(d, L);
+    HubSliceAddr ad{p.hub_base[blockIdx.x] + (int64_t)(tid >> 5) * W * G + (tid & 31), W};
+    const int ng = (int)((len + 3) >> 2);
+    fold_groups<ModAcc, WT, false>(acc, p.sl_idx, p.sl_w, labels, v, (int)len, ng, ng, ad);
+  }
   s_k[tid] = acc.k();
   s_in[tid] = acc.in();
   __syncthreads();
@@ -186,35 +196,158 @@ __global__ void __launch_bounds__(256) sigma_sq_kernel(const double* sigma_c, in
   if (threadIdx.x == 0) sq[blockIdx.x] = s[0];
 }
 
-// Fixed-order final sums; out4 = {2m, intra weight, sum_c Sigma_c^2, Q}.
-__global__ void __launch_bounds__(256) modularity_total_kernel(const double* slots,
-                                                              const double* sq, double* out4) {
-  __shared__ double sa[256], sb[256], sc[256];
+// Fixed-order final sums; out4 = {2m, intra weight, sum_c Sigma_c^2, Q}.  a, b, c hold
+// na, na, nc partial sums of 2m, the intra-community weight and Sigma_c^2 (a and b read
+// with stride sa).
+__global__ void __launch_bounds__(256) modularity_total_kernel(const double* a_part,
+                                                              const double* b_part, int sa,
+                                                              int na, const double* c_part,
+                                                              int nc, double* out4) {
+  __shared__ double sa_[256], sb_[256], sc_[256];
   double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < kModSlots; i += 256) {
-    a += slots[2 * i];
-    b += slots[2 * i + 1];
+  for (int i = threadIdx.x; i < na; i += 256) {
+    a += a_part[(int64_t)sa * i];
+    b += b_part[(int64_t)sa * i];
   }
-  for (int i = threadIdx.x; i < kSqBlocks; i += 256) c += sq[i];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  sc[threadIdx.x] = c;
+  for (int i = threadIdx.x; i < nc; i += 256) c += c_part[i];
+  sa_[threadIdx.x] = a;
+  sb_[threadIdx.x] = b;
+  sc_[threadIdx.x] = c;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
-      sa[threadIdx.x] += sa[threadIdx.x + h];
-      sb[threadIdx.x] += sb[threadIdx.x + h];
-      sc[threadIdx.x] += sc[threadIdx.x + h];
+      sa_[threadIdx.x] += sa_[threadIdx.x + h];
+      sb_[threadIdx.x] += sb_[threadIdx.x + h];
+      sc_[threadIdx.x] += sc_[threadIdx.x + h];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double two_m = sa[0];
+    const double two_m = sa_[0];
     out4[0] = two_m;
-    out4[1] = sb[0];
-    out4[2] = sc[0];
-    out4[3] = two_m > 0.0 ? sb[0] / two_m - sc[0] / (two_m * two_m) : 0.0;
+    out4[1] = sb_[0];
+    out4[2] = sc_[0];
+    out4[3] = two_m > 0.0 ? sb_[0] / two_m - sc_[0] / (two_m * two_m) : 0.0;
   }
+}
+
+// ------------------------------------------------------- standalone pass (no binning)
+//
+// A warp takes a tile of 32 consecutive vertices.  A row of at most kModShortRow
+// positions is summed by its own lane; a longer row is cut into 32 contiguous pieces, one
+// per lane, summed by the whole warp afterwards.  K_i and the intra-community weight stay
+// in each lane's registers until the end, then go through a fixed-order block tree into
+// one partial per block; only the Sigma_c atomics depend on timing.
+
+constexpr int kModThreads = 256;
+constexpr int kModMaxBlocks = 152 * 3;  // one wave at 3 CTAs per SM (78 registers)
+constexpr int kModShortRow = 32;
+
+// Positions [b, e) of a row into acc: the pipelined 16-byte reads of the sweep when both
+// arrays start on a 16-byte boundary (VEC), else one entry at a time.
+template <bool WT, bool VEC>
+__device__ __forceinline__ void mod_range(ModAcc& acc, const int32_t* __restrict__ idx,
+                                          const float* __restrict__ wts,
+                                          const int32_t* __restrict__ labels, int64_t m,
+                                          int v, int64_t b, int64_t e) {
+  if constexpr (VEC) {
+    fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, b, e);
+  } else {
+    for (int64_t p = b; p < e; ++p) {
+      const float x = WT ? __ldg(wts + p) : 1.f;
+      if (x > 0.f) acc.add(__ldg(labels + __ldg(idx + p)), x);
+    }
+  }
+}
+
+template <bool WT, bool VEC>
+__global__ void __launch_bounds__(kModThreads, 3) modularity_rows_kernel(
+    const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
+    const float* __restrict__ wts, int64_t m, const int32_t* __restrict__ labels, int32_t n,
+    double* sigma_c, double* part_k, double* part_in) {
+  __shared__ double s_k[kModThreads], s_in[kModThreads];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t ntiles = ((int64_t)n + 31) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kModThreads / 32);
+  double tot_k = 0.0, tot_in = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * (kModThreads / 32) + (tid >> 5); t < ntiles;
+       t += nwarps) {
+    const int64_t v = t * 32 + lane;
+    const bool own = v < n;
+    int64_t b = 0, e = 0;
+    int cv = -1;
+    if (own) {
+      b = __ldg(off + v);
+      e = __ldg(off + v + 1);
+      cv = __ldg(labels + v);
+    }
+    ModAcc acc{0.f, 0.f, 0.f, 0.f, cv};
+    const bool longrow = e - b > kModShortRow;
+    if (own && !longrow) mod_range<WT, VEC>(acc, idx, wts, labels, m, (int)v, b, e);
+    double kv = acc.k(), in = acc.in();
+    for (unsigned lm = __ballot_sync(kFullMask, longrow); lm; lm &= lm - 1) {
+      const int src = __ffs(lm) - 1;
+      const int64_t rb = __shfl_sync(kFullMask, b, src);
+      const int64_t d = __shfl_sync(kFullMask, e, src) - rb;
+      ModAcc pa{0.f, 0.f, 0.f, 0.f, __shfl_sync(kFullMask, cv, src)};
+      mod_range<WT, VEC>(pa, idx, wts, labels, m, (int)(t * 32 + src), rb + (lane * d) / 32,
+                         rb + ((lane + 1) * d) / 32);
+      double sk = pa.k(), si = pa.in();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sk += __shfl_xor_sync(kFullMask, sk, o);
+        si += __shfl_xor_sync(kFullMask, si, o);
+      }
+      if (lane == src) {
+        kv = sk;
+        in = si;
+      }
+    }
+    tot_k += kv;
+    tot_in += in;
+    s_k[tid] = kv;
+    __syncwarp();
+    const unsigned grp = __match_any_sync(kFullMask, own ? cv : -(lane + 2));
+    if (own && lane == __ffs(grp) - 1) {
+      double sum = 0.0;
+      for (unsigned g = grp; g; g &= g - 1) sum += s_k[(tid & ~31) + __ffs(g) - 1];
+      if (sum != 0.0) atomicAdd(sigma_c + cv, sum);
+    }
+    __syncwarp();
+  }
+  s_k[tid] = tot_k;
+  s_in[tid] = tot_in;
+  __syncthreads();
+  for (int h = kModThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      s_k[tid] += s_k[tid + h];
+      s_in[tid] += s_in[tid + h];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    part_k[blockIdx.x] = s_k[0];
+    part_in[blockIdx.x] = s_in[0];
+  }
+}
+
+int mod_row_blocks(int32_t n) {
+  const int64_t b = (((int64_t)n + 31) / 32 + kModThreads / 32 - 1) / (kModThreads / 32);
+  return (int)(b < 1 ? 1 : (b > kModMaxBlocks ? kModMaxBlocks : b));
+}
+
+int mod_sq_blocks(int32_t n) {
+  const int64_t b = ((int64_t)n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > kModMaxBlocks ? kModMaxBlocks : b));
+}
+
+template <bool WT, bool VEC>
+void launch_rows(const int64_t* off, const int32_t* idx, const float* w, int64_t m,
+                 const int32_t* labels, int32_t n, double* sigma_c, double* part_k,
+                 double* part_in, cudaStream_t s) {
+  modularity_rows_kernel<WT, VEC><<<mod_row_blocks(n), kModThreads, 0, s>>>(
+      off, idx, w, m, labels, n, sigma_c, part_k, part_in);
+  count_launch();
 }
 
 // Batch: Q of graph g from its totals and the Sigma_c of its label range (one block per
@@ -274,6 +407,7 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
     if (cnt <= 0) continue;
     WarpPlan q = p;
     q.hub_desc = p.hub_desc + p.hub_start[c];
+    q.hub_base = p.hub_base + p.hub_start[c];
     if (w)
       modularity_hub_kernel<true><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
     else
@@ -292,7 +426,39 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
   }
   sigma_sq_kernel<<<kSqBlocks, 256, 0, s>>>(sigma_c, n, sq);
   count_launch();
-  modularity_total_kernel<<<1, 256, 0, s>>>(slots, sq, out4);
+  modularity_total_kernel<<<1, 256, 0, s>>>(slots, slots + 1, 2, kModSlots, sq, kSqBlocks,
+                                             out4);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int modularity_partials(int32_t n) {
+  const int r = mod_row_blocks(n), q = mod_sq_blocks(n);
+  return r > q ? r : q;
+}
+
+cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const float* w, int64_t m,
+                              const int32_t* labels, int32_t n, double* sigma_c,
+                              double* partials, int32_t npart, double* out4, cudaStream_t s) {
+  double* part_k = partials;
+  double* part_in = partials + npart;
+  double* sq = partials + 2 * (int64_t)npart;
+  int nr = 0, nq = 0;
+  if (n > 0) {
+    const int64_t zb = ((int64_t)n + 255) / 256;
+    zero_f64_kernel<<<(unsigned)(zb < 152 * 8 ? zb : 152 * 8), 256, 0, s>>>(sigma_c, n);
+    count_launch();
+    const bool vec = ((uintptr_t)idx & 15) == 0 && ((uintptr_t)w & 15) == 0;
+    if (w != nullptr && vec) launch_rows<true, true>(off, idx, w, m, labels, n, sigma_c, part_k, part_in, s);
+    else if (w != nullptr) launch_rows<true, false>(off, idx, w, m, labels, n, sigma_c, part_k, part_in, s);
+    else if (vec) launch_rows<false, true>(off, idx, w, m, labels, n, sigma_c, part_k, part_in, s);
+    else launch_rows<false, false>(off, idx, w, m, labels, n, sigma_c, part_k, part_in, s);
+    nr = mod_row_blocks(n);
+    nq = mod_sq_blocks(n);
+    sigma_sq_kernel<<<nq, 256, 0, s>>>(sigma_c, n, sq);
+    count_launch();
+  }
+  modularity_total_kernel<<<1, 256, 0, s>>>(part_k, part_in, 1, nr, sq, nq, out4);
   count_launch();
   return cudaGetLastError();
 }

@@ -50,8 +50,8 @@ extern "C" lpa_status lpa_modularity_noalloc(const int64_t* offsets, const int32
                                              const int32_t* labels, double* q_out,
                                              const lpa_options* opt) {
   char msg[256];
-  if (n < 0 || m < 0 || !offsets || (m > 0 && !indices) || (n > 0 && !labels) || !q_out)
-    return (lpa_status)lpa::set_last_error(LPA_EINVAL, "bad argument (NULL pointer or negative size)");
+  const int chk = lpa::check_modularity_args(offsets, indices, n, m, labels, q_out);
+  if (chk != LPA_OK) return (lpa_status)chk;
   if (n > LPA_NOALLOC_MAX_N) {
     snprintf(msg, sizeof(msg), "n = %d exceeds the static scratch limit of %d vertices", n,
              LPA_NOALLOC_MAX_N);
@@ -82,10 +82,10 @@ extern "C" lpa_status lpa_modularity_noalloc(const int64_t* offsets, const int32
       return (lpa_status)lpa::set_last_error(LPA_EINVAL, msg);
     }
   }
-  // launch_modularity zeroes Sigma_c and the partials before accumulating, so the
-  // contents left by an earlier call do not matter
+  // launch_modularity clears Sigma_c before accumulating and writes every partial it
+  // reads, so the contents left by an earlier call do not matter
   double host_out[4] = {0, 0, 0, 0};
-  e = lpa::launch_modularity(offsets, indices, weights, labels, n, sigma_c, partials, npart, out4, s);
+  e = lpa::launch_modularity(offsets, indices, weights, m, labels, n, sigma_c, partials, npart, out4, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out4, sizeof(host_out), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return (lpa_status)lpa::set_last_error(LPA_ECUDA, cudaGetErrorString(e));

@@ -1,6 +1,6 @@
 // lpa_setup.cu -- everything around the sweep: CSR validation, degree binning into
-// chunks and hubs, label initialisation, the on-device convergence test (Alg. 1, `lpa`),
-// and modularity (Eq. 1).
+// chunks and hubs, label initialisation and the on-device convergence test (Alg. 1,
+// `lpa`).
 #include "lpa_internal.cuh"
 
 namespace lpa {
@@ -177,20 +177,16 @@ __global__ void __launch_bounds__(kScanThreads) scan3_kernel(int64_t* a, int64_t
 
 // ------------------------------------------------- binning for the warp sweep
 
-// Sort key of a vertex with d positions starting at CSR position b inside its window: its
-// class c < kHubClasses for a hub; kHubClasses + c for mid class c (larger L and longer
-// leaves first); for a one-leaf row kHubClasses + kMidClasses + (kLowKeys - 1 -
-// min(a, kLowKeys - 1)) with a = d + (b mod 4), the
-// row's span in 16-byte groups' positions, so the rows of a warp read the same number of
-// aligned groups (longer spans first).
-__device__ __forceinline__ int window_key(int64_t d, int64_t b, int e0, int lmax) {
+// Sort key of a vertex with d positions inside its window: its class c < kHubClasses for a
+// hub; kHubClasses + c for mid class c (larger L and longer leaves first); for a one-leaf
+// row kHubClasses + kMidClasses + (kLowKeys - 1 - min(d, kLowKeys - 1)), so the rows of a
+// warp have (nearly) the same number of groups in the sliced copy (longer rows first).
+__device__ __forceinline__ int window_key(int64_t d, int e0, int lmax) {
   const int L = leaf_count(d, e0, lmax);
   if (d > kHubDegree || L > kMaxWarpLeaves)  // hub class c: CTA of 256 >> c threads
     return L >= 256 ? 0 : (L == 128 ? 1 : (L == 64 ? 2 : 3));
-  if (L == 1) {
-    const int64_t a = d + (b & 3);
-    return kHubClasses + kMidClasses + (kLowKeys - 1 - (int)(a < kLowKeys ? a : kLowKeys - 1));
-  }
+  if (L == 1)
+    return kHubClasses + kMidClasses + (kLowKeys - 1 - (int)(d < kLowKeys ? d : kLowKeys - 1));
   const int lidx = 5 - (31 - __clz(L));  // L = 32 -> 0 ... L = 2 -> 4
   int sub = (int)(((d / L) * 4) / e0) - 4;  // leaf length quarter in [e0, 2 e0)
   sub = sub < 0 ? 0 : (sub > kMidSub - 1 ? kMidSub - 1 : sub);
@@ -227,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
       b[q] = off[v];
       const int64_t dd = off[v + 1] - b[q];
       d[q] = (int)dd;  // rows above INT32_MAX are refused after binning
-      key[q] = window_key(dd, b[q], e0, lmax);
+      key[q] = window_key(dd, e0, lmax);
       atomicAdd(&s_hist[key[q]], 1);
     }
   }
@@ -454,108 +450,91 @@ __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long value,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = value;
 }
 
-// ------------------------------------------------------------------ modularity
+// ------------------------------------------------- sliced copy of the CSR
 
-constexpr int kModThreads = 256;
-constexpr int kModBlocks = 152 * 8;
+// Pass 1: the groups of each lane warp's slice (the sum of its lanes' ceil(len / 4)) and
+// of each hub's slice (L leaves x the groups of its longest leaf).
+__global__ void __launch_bounds__(256) slice_count_kernel(const int4* __restrict__ lane_desc,
+                                                         int64_t nlanes,
+                                                         const int4* __restrict__ hub_desc,
+                                                         int32_t nhubs, int e0, int lmax,
+                                                         int32_t* cnt) {
+  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t nw = nlanes >> 5;
+  if (t < nlanes) {  // whole warps: nlanes is a multiple of 32
+    const int4 l = __ldg(lane_desc + t);
+    const int g = l.x >= 0 ? ((l.w & ((1 << kLaneLeafShift) - 1)) + 3) >> 2 : 0;
+    const int sum = __reduce_add_sync(0xffffffffu, g);
+    if ((threadIdx.x & 31) == 0) cnt[t >> 5] = sum;
+  }
+  const int64_t h = t - (((nlanes + 255) >> 8) << 8);  // hubs after the lane blocks
+  if (h >= 0 && h < nhubs) {
+    const int64_t d = __ldg(hub_desc + h).w;
+    const int L = leaf_count(d, e0, lmax);
+    cnt[nw + h] = (int32_t)(L * hub_leaf_groups(d, L));
+  }
+}
 
-__device__ __forceinline__ double warp_sum(double x) {
+// One group of four positions [g, g + 4) of the CSR, of which the first `valid` belong to
+// the leaf; the rest become {self, weight 0}.
+template <bool WT>
+__device__ __forceinline__ void copy_group(const int32_t* __restrict__ idx,
+                                           const float* __restrict__ w, int64_t g,
+                                           int64_t valid, int self, int4* si, float4* sw,
+                                           int64_t p) {
+  int j[4];
+  float x[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
+  for (int u = 0; u < 4; ++u) {
+    j[u] = u < valid ? __ldg(idx + g + u) : self;
+    x[u] = u < valid ? (WT ? __ldg(w + g + u) : 1.f) : 0.f;
+  }
+  si[p] = make_int4(j[0], j[1], j[2], j[3]);
+  if (WT) sw[p] = make_float4(x[0], x[1], x[2], x[3]);
 }
 
-// Pass 1: a warp walks 32 consecutive vertices at a time, lanes striding over each row:
-// K_i and the intra-community weight; Sigma_c += K_i, with consecutive vertices of the
-// same label merged into one atomic (labels of neighbouring ids usually agree).
-__global__ void __launch_bounds__(kModThreads) modularity_rows_kernel(
-    const int64_t* off, const int32_t* idx, const float* w, const int32_t* labels, int32_t n,
-    double* sigma_c, double* partials) {
-  __shared__ double s_k[kModThreads / 32], s_in[kModThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * (kModThreads / 32);
-  double acc_k = 0.0, acc_in = 0.0;
-  int run_c = -1;
-  double run_s = 0.0;
-  for (int64_t base = ((int64_t)blockIdx.x * (kModThreads / 32) + wid) * 32; base < n;
-       base += nwarps * 32) {
-    const int64_t vend = base + 32 < n ? base + 32 : n;
-    for (int64_t v = base; v < vend; ++v) {
-      const int cv = labels[v];
-      double kv = 0.0, in = 0.0;
-      for (int64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
-        const double x = w ? (double)w[p] : 1.0;
-        kv += x;
-        if (labels[idx[p]] == cv) in += x;
-      }
-      kv = warp_sum(kv);
-      in = warp_sum(in);
-      if (lane == 0) {
-        if (cv != run_c) {
-          if (run_c >= 0 && run_s != 0.0) atomicAdd(sigma_c + run_c, run_s);
-          run_c = cv;
-          run_s = 0.0;
-        }
-        run_s += kv;
-        acc_k += kv;
-        acc_in += in;
-      }
-    }
-  }
-  if (lane == 0) {
-    if (run_c >= 0 && run_s != 0.0) atomicAdd(sigma_c + run_c, run_s);
-    s_k[wid] = acc_k;
-    s_in[wid] = acc_in;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < kModThreads / 32; ++i) {
-      a += s_k[i];
-      b += s_in[i];
-    }
-    partials[3 * blockIdx.x + 0] = a;
-    partials[3 * blockIdx.x + 1] = b;
+// Pass 2, lane warps: each lane copies its leaf into the columns of its warp's slice.
+template <bool WT>
+__global__ void __launch_bounds__(256) slice_fill_lanes_kernel(
+    const int32_t* __restrict__ idx, const float* __restrict__ w,
+    const int4* __restrict__ lane_desc, int64_t nlanes, const int64_t* __restrict__ base,
+    int4* si, float4* sw) {
+  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (t >= nlanes) return;  // whole warps
+  const int lane = threadIdx.x & 31;
+  const int4 l = __ldg(lane_desc + t);
+  const int v = l.x;
+  const int64_t lo = (int64_t)(uint32_t)l.y | ((int64_t)l.z << 32);
+  const int64_t len = v >= 0 ? (l.w & ((1 << kLaneLeafShift) - 1)) : 0;
+  const int ng = (int)((len + 3) >> 2);
+  const int iters = __reduce_max_sync(0xffffffffu, ng);
+  int64_t col = base[t >> 5];
+  for (int k = 0; k < iters; ++k) {
+    const unsigned has = __ballot_sync(0xffffffffu, ng > k);
+    if (ng > k) copy_group<WT>(idx, w, lo + 4 * k, len - 4 * k, v, si, sw,
+                               col + __popc(has & ((1u << lane) - 1u)));
+    col += __popc(has);
   }
 }
 
-// Pass 2: sum over communities of Sigma_c^2.
-__global__ void __launch_bounds__(kModThreads) modularity_sq_kernel(const double* sigma_c, int32_t n,
-                                                                    double* partials) {
-  __shared__ double s[kModThreads / 32];
-  double acc = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * kModThreads;
-  for (int64_t c = (int64_t)blockIdx.x * kModThreads + threadIdx.x; c < n; c += stride)
-    acc += sigma_c[c] * sigma_c[c];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int i = 0; i < kModThreads / 32; ++i) a += s[i];
-    partials[3 * blockIdx.x + 2] = a;
+// Pass 2, hubs: a CTA per hub, leaf t on thread t.
+template <bool WT>
+__global__ void __launch_bounds__(kThreads) slice_fill_hubs_kernel(
+    const int32_t* __restrict__ idx, const float* __restrict__ w,
+    const int4* __restrict__ hub_desc, const int64_t* __restrict__ base, int e0, int lmax,
+    int4* si, float4* sw) {
+  const int4 h = __ldg(hub_desc + blockIdx.x);
+  const int64_t b = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
+  const int64_t d = h.w;
+  const int L = leaf_count(d, e0, lmax);
+  const int64_t G = hub_leaf_groups(d, L);
+  const int W = L < 32 ? L : 32;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    const int64_t lo = b + (t * d) / L, len = b + ((t + 1) * d) / L - lo;
+    const int64_t first = base[blockIdx.x] + (int64_t)(t >> 5) * W * G + (t & 31);
+    for (int64_t k = 0; k < G; ++k)
+      copy_group<WT>(idx, w, lo + 4 * k, len - 4 * k, h.x, si, sw, first + k * W);
   }
-}
-
-// Fixed-order final reduction of the per-block partials.
-__global__ void modularity_final_kernel(const double* partials, int32_t npart, double* out3) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = 0; i < npart; ++i) {
-    a += partials[3 * i + 0];
-    b += partials[3 * i + 1];
-    c += partials[3 * i + 2];
-  }
-  out3[0] = a;
-  out3[1] = b;
-  out3[2] = c;
-  // Eq. 1: Q = sum_c sigma_c / 2m - sum_c (Sigma_c / 2m)^2
-  out3[3] = a > 0.0 ? b / a - c / (a * a) : 0.0;
-}
-
-__global__ void fill_f64_kernel(double* p, int64_t count) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = 0.0;
 }
 
 inline unsigned grid_for(int64_t work, int threads, unsigned cap = 152 * 16) {
@@ -681,32 +660,43 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
   return cudaGetLastError();
 }
 
-int modularity_partials(int32_t n) {
-  (void)n;
-  return kModBlocks;
-}
-
-cudaError_t launch_modularity(const int64_t* off, const int32_t* idx, const float* w,
-                              const int32_t* labels, int32_t n, double* sigma_c, double* partials,
-                              int32_t npart, double* out3, cudaStream_t s) {
-  fill_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(sigma_c, n);
-  count_launch();
-  fill_f64_kernel<<<grid_for(3 * (int64_t)npart, 256), 256, 0, s>>>(partials, 3 * (int64_t)npart);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (n > 0) {
-    modularity_rows_kernel<<<npart, kModThreads, 0, s>>>(off, idx, w, labels, n, sigma_c, partials);
+cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
+                               cudaStream_t s) {
+  const int64_t nw = p.nlanes >> 5;
+  const int64_t threads = ((p.nlanes + 255) >> 8 << 8) + p.nhubs;
+  if (threads > 0) {
+    slice_count_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        p.lane_desc, p.nlanes, p.hub_desc, p.nhubs, e0, lmax, cnt);
     count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    modularity_sq_kernel<<<npart, kModThreads, 0, s>>>(sigma_c, n, partials);
-    count_launch();
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  modularity_final_kernel<<<1, 32, 0, s>>>(partials, npart, out3);
-  count_launch();
+  return launch_scan_counts(cnt, nw + p.nhubs, base, s);
+}
+
+cudaError_t launch_slice_fill(const int32_t* idx, const float* w, const WarpPlan& p, int e0,
+                              int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s) {
+  if (p.nlanes > 0) {
+    const unsigned grid = (unsigned)((p.nlanes + 255) / 256);
+    if (w)
+      slice_fill_lanes_kernel<true><<<grid, 256, 0, s>>>(idx, w, p.lane_desc, p.nlanes,
+                                                         p.lane_base, sl_idx, sl_w);
+    else
+      slice_fill_lanes_kernel<false><<<grid, 256, 0, s>>>(idx, w, p.lane_desc, p.nlanes,
+                                                          p.lane_base, sl_idx, sl_w);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (p.nhubs > 0) {
+    if (w)
+      slice_fill_hubs_kernel<true><<<p.nhubs, kThreads, 0, s>>>(idx, w, p.hub_desc, p.hub_base,
+                                                                e0, lmax, sl_idx, sl_w);
+    else
+      slice_fill_hubs_kernel<false><<<p.nhubs, kThreads, 0, s>>>(idx, w, p.hub_desc, p.hub_base,
+                                                                 e0, lmax, sl_idx, sl_w);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

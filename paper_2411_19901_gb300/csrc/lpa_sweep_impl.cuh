@@ -12,9 +12,10 @@
 //  * hubs (longer rows, or more than 32 leaves): one CTA, one leaf per thread, shuffles
 //    within warps, shared memory across warps (a kernel of their own, so the lane kernel
 //    runs CTAs of single warps that retire independently).
-// Every lane reads its range with the pipelined fold of lpa_fold.cuh (16-byte index and
-// weight loads two groups ahead, label gathers one group ahead).  The tree depends only
-// on the row length, so results never depend on which of these paths a vertex takes.
+// Every lane reads its leaf from the plan's sliced copy of the CSR with the pipelined fold
+// of lpa_fold.cuh (16-byte index and weight loads two groups ahead, the lanes of a warp
+// side by side; label gathers one group ahead).  The tree depends only on the row length,
+// so results never depend on which of these paths a vertex takes.
 #pragma once
 
 #include "lpa_fold.cuh"
@@ -67,9 +68,14 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
   const int own = a.c_prev[v];
   S st;
   st.init(own);
-  if (tid < L)
-    fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, v, base + (tid * d) / L,
-                                   base + ((tid + 1) * d) / L);
+  if (tid < L) {
+    const int64_t lo = base + (tid * d) / L, len = base + ((tid + 1) * d) / L - lo;
+    const int W = L < 32 ? L : 32;
+    const int64_t G = hub_leaf_groups(d, L);
+    HubSliceAddr ad{p.hub_base[blockIdx.x] + (int64_t)(tid >> 5) * W * G + (tid & 31), W};
+    const int ng = (int)((len + 3) >> 2);
+    fold_groups<S, WT, true>(st, p.sl_idx, p.sl_w, a.c_prev, v, (int)len, ng, ng, ad);
+  }
   const int Lw = L < 32 ? L : 32;
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
   if (L > 32) cross_warp_tree<S>(st, L, tid, sk, sv);
@@ -159,10 +165,15 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
   if (v >= 0) {
     own = a.c_prev[v];
     st.init(own);
-    if (act) fold_range<S, WT, true>(st, a.idx, a.w, a.c_prev, a.m, v, lo, lo + len);
   } else {
     st.init(-1);
   }
+  // the leaf from the sliced copy: every lane of the warp runs the warp's longest leaf's
+  // steps (the slice places are decided by warp votes)
+  const int ngl = (int)((len + 3) >> 2);
+  LaneSliceAddr ad{q < p.nlanes ? p.lane_base[q >> 5] : 0, ngl, (1u << lane) - 1u};
+  fold_groups<S, WT, true>(st, p.sl_idx, p.sl_w, a.c_prev, v, (int)len, act ? ngl : 0,
+                           __reduce_max_sync(kFullMask, ngl), ad);
   const int Lw = __reduce_max_sync(kFullMask, L);
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, v >= 0 && s < L && (leaf & (2 * s - 1)) == 0);
   int choice = -1;
@@ -222,6 +233,7 @@ cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream
     if (cnt <= 0) continue;
     WarpPlan q = p;
     q.hub_desc = p.hub_desc + p.hub_start[c];
+    q.hub_base = p.hub_base + p.hub_start[c];
     sweep_hub_kernel<S, WT, RESCAN><<<(unsigned)cnt, kThreads >> c, 0, s_hub>>>(a, q);
     count_launch();
   }

@@ -1,6 +1,7 @@
 // lpa_sweep_variants.cu -- the MG ablation axes of the paper: the paper-literal
 // accumulate of Alg. 2 (LPA_MG_UNCLAMPED) and the double scan of Sec. 4.4 (LPA_RESCAN),
-// for every k.  A translation unit of their own so they compile beside the main sweep.
+// for k <= 8 here and k = 16, 32 in lpa_sweep_variants_k16.cu / _k32.cu (translation
+// units of their own so they compile in parallel beside the main sweep).
 #include "lpa_sweep_impl.cuh"
 
 namespace lpa {
@@ -13,8 +14,8 @@ cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, bool weigh
     case 2: return launch_mg_variant<2>(literal, rescan, weighted, a, p, s, s_hub);
     case 4: return launch_mg_variant<4>(literal, rescan, weighted, a, p, s, s_hub);
     case 8: return launch_mg_variant<8>(literal, rescan, weighted, a, p, s, s_hub);
-    case 16: return launch_mg_variant<16>(literal, rescan, weighted, a, p, s, s_hub);
-    case 32: return launch_mg_variant<32>(literal, rescan, weighted, a, p, s, s_hub);
+    case 16: return launch_sweep_mg16_variant(literal, rescan, weighted, a, p, s, s_hub);
+    case 32: return launch_sweep_mg32_variant(literal, rescan, weighted, a, p, s, s_hub);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+from tolerance import q_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -121,6 +122,6 @@ def test_batch_modularity_per_graph(lpa):
         ref = oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG, threads=4)
         assert np.array_equal(labels[i], ref["labels"]), i
         q = oracle.modularity(g.offsets, g.indices, g.weights, ref["labels"]) if g.n else 0.0
-        assert abs(stats[i]["modularity"] - q) <= 1e-9 * max(abs(q), 1e-3), (i, stats[i], q)
+        assert q_close(stats[i]["modularity"], q), (i, stats[i], q)
     with pytest.raises(lpa.LpaError, match="sketch mode"):
         run_batch(lpa, gs[:3], "exact", modularity=True)

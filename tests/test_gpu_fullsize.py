@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tolerance import q_close
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -74,7 +75,7 @@ def test_full_size_sweeps_and_run(lpa, name):
     got = labels.cpu().numpy()
     assert np.array_equal(got, ref["labels"]), np.nonzero(got != ref["labels"])[0][:10]
     q = oracle.modularity(g.offsets, g.indices, g.weights, ref["labels"])
-    assert abs(st["modularity"] - q) <= 1e-9 * max(abs(q), 1e-3), (st["modularity"], q)
+    assert q_close(st["modularity"], q), (st["modularity"], q)
 
 
 def banded_graph(n, half):

@@ -12,12 +12,12 @@ import pytest
 
 import oracle
 import synth
+from tolerance import q_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 OMODE = {"exact": oracle.EXACT, "mg": oracle.MG, "bm": oracle.BM}
-Q_RTOL = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -40,8 +40,6 @@ def to_dev(g):
     return off, idx, w
 
 
-def q_close(a, b):
-    return abs(a - b) <= Q_RTOL * max(abs(b), 1e-3)
 
 
 # graphs that reach every kernel path: short rows (one leaf), 2..32 leaves in chunks,
