@@ -461,11 +461,26 @@ def run_ours(args):
     d_idx = h_idx.to(dev)
     d_w = h_w.to(dev) if weighted else None
     labels = torch.empty(n, dtype=torch.int32, device=dev)
-    ws = torch.empty(lpa.lpa_workspace_size(n, m, args.mode, args.k), dtype=torch.uint8,
-                     device=dev)
     stream = torch.cuda.current_stream(dev)
-    opt = lpa.make_options(validate=False, timing=True, modularity=True, stream=stream,
-                           workspace=ws, unclamped=args.unclamped, rescan=args.rescan)
+    # the launch choices: the defaults, or with --tune the tuner's pick for this graph
+    # (timed before the timed region; results are identical under every choice)
+    tuning, tune_table, tune_s = None, None, 0.0
+    if args.tune:
+        from paper_2411_19901_gb300 import tune as _tune
+
+        t0 = time.perf_counter()
+        tuning, tune_table = _tune.tune_graph(d_off, d_idx, d_w, mode=args.mode, k=args.k,
+                                              reps=1, stream=stream)
+        tune_s = time.perf_counter() - t0
+
+    def options(tun, **kw):
+        return lpa.make_options(validate=False, stream=stream, unclamped=args.unclamped,
+                                rescan=args.rescan, tuning=tun, **kw)
+
+    ws_bytes = max(lpa.lpa_workspace_size_ex(n, m, args.mode, args.k, options(t))
+                   for t in (None, tuning))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    opt = options(tuning, timing=True, modularity=True, workspace=ws)
 
     def step():
         st = lpa.lpa_stats()
@@ -507,9 +522,7 @@ def run_ours(args):
         st = lpa.lpa_stats()
         lpa.lpa_detect_host(h_off.numpy(), h_idx.numpy(), h_w.numpy() if weighted else None,
                             n, m, args.mode, args.k, 0.05, 20, h_lab.numpy(), st,
-                            lpa.make_options(validate=False, modularity=True, stream=stream,
-                                             workspace=ws, unclamped=args.unclamped,
-                                             rescan=args.rescan))
+                            options(tuning, modularity=True, workspace=ws))
         return st.to_dict()
 
     e2e_call()
@@ -526,6 +539,28 @@ def run_ours(args):
     e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
     barrier()
     e2e_edges = sum(s["iterations"] * m for s in e2e_stats)
+
+    # with --tune, the same steps under the default launch choices, for comparison
+    fixed = None
+    if args.tune:
+        fopt = options(None, timing=True, modularity=True, workspace=ws)
+        lpa.lpa_detect_ex(d_off, d_idx, d_w, n, m, args.mode, args.k, 0.05, 20, labels,
+                          lpa.lpa_stats(), fopt)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        f0.record(stream)
+        fst = []
+        for _ in range(args.steps):
+            st = lpa.lpa_stats()
+            lpa.lpa_detect_ex(d_off, d_idx, d_w, n, m, args.mode, args.k, 0.05, 20, labels, st,
+                              fopt)
+            fst.append(st.to_dict())
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1)
+        fixed = {"value": sum(s["iterations"] * m for s in fst) / (fms * 1e-3),
+                 "ms_per_step": fms / args.steps,
+                 "sweep_ms": sum(s["sweep_ms"] for s in fst) / max(sum(s["iterations"] for s in fst), 1)}
 
     # the standalone modularity entry point (Eq. 1) on the final labels, outside the timed
     # region: CUDA events around lpa_modularity_ex calls, after one untimed call
@@ -591,6 +626,10 @@ def run_ours(args):
         "iterations": [s["iterations"] for s in stats],
         "sweep_ms_iter": [round(x, 3) for x in stats[-1]["sweep_ms_iter"]],
         "modularity": stats[-1]["modularity"],
+        "tuning": ({"chosen": tuning, "tuner_s": tune_s, "candidates": len(tune_table),
+                    "fixed_defaults": fixed,
+                    "table": [[r["tuning"], round(r["ms"], 3)] for r in tune_table]}
+                   if args.tune else {"chosen": "defaults"}),
         "modularity_standalone": {"ms": mod_ms, "q": q_alone, "algorithmic_bytes": mod_bytes,
                                   "achieved_gbs": mod_bytes / (mod_ms * 1e-3) / 1e9,
                                   "call": "lpa_modularity_ex (no plan), mean of 3"},
@@ -647,10 +686,18 @@ def run_batch(args):
     d = [(o.to(dev), i.to(dev), None, torch.empty(g.n, dtype=torch.int32, device=dev))
          for (o, i), g in zip(h, gs)]
     stream = torch.cuda.current_stream(dev)
-    opt = lpa.make_options(validate=False, stream=stream)
+    tuning, tune_table, tune_s = None, None, 0.0
+    if args.tune:  # the tuner's pick for this batch, timed before the timed region
+        from paper_2411_19901_gb300 import tune as _tune
 
-    def step():
-        return lpa.lpa_batch_detect(d, mode=args.mode, k=8, tol=0.05, max_iter=20, opt=opt)
+        t0 = time.perf_counter()
+        tuning, tune_table = _tune.tune_batch(d, mode=args.mode, k=8, reps=1, stream=stream)
+        tune_s = time.perf_counter() - t0
+    opt = lpa.make_options(validate=False, stream=stream, tuning=tuning)
+
+    def step(o=None):
+        return lpa.lpa_batch_detect(d, mode=args.mode, k=8, tol=0.05, max_iter=20,
+                                    opt=o or opt)
 
     for _ in range(args.warmup):
         step()
@@ -672,6 +719,19 @@ def run_batch(args):
     launches = lpa.lpa_launch_count() - launches0
     elapsed_ms = ev0.elapsed_time(ev1)
     stats = results[-1][0]
+    fixed = None
+    if args.tune:  # the same steps under the default launch choices
+        fopt = lpa.make_options(validate=False, stream=stream)
+        step(fopt)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        f0.record(stream)
+        for _ in range(args.steps):
+            step(fopt)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1) / args.steps
+        fixed = {"value": count / (fms * 1e-3), "ms_per_step": fms}
     # one call per graph (the same work, one plan and run per graph)
     one_steps = 1
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -742,6 +802,10 @@ def run_batch(args):
         "gpu_launches": launches,
         "clocks": clk,
         "iterations_max": max(iters), "iterations_mean": sum(iters) / len(iters),
+        "tuning": ({"chosen": tuning, "tuner_s": tune_s, "candidates": len(tune_table),
+                    "fixed_defaults": fixed,
+                    "table": [[r["tuning"], round(r["ms"], 3)] for r in tune_table]}
+                   if args.tune else {"chosen": "defaults"}),
         "generate_s": gen_s,
     }
     print(json.dumps(line), flush=True)
@@ -952,6 +1016,9 @@ def main():
                     help="MG ablation: the accumulate exactly as printed (LPA_MG_UNCLAMPED)")
     ap.add_argument("--rescan", action="store_true",
                     help="MG ablation: the double scan of Sec. 4.4 (LPA_RESCAN)")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the autotuner's candidates first and run the timed steps with "
+                         "its pick (the default launch choices are timed beside it)")
     args = ap.parse_args()
     if args.mode != "mg" and (args.k != 8 or args.unclamped or args.rescan):
         ap.error("--k, --unclamped and --rescan apply to --mode mg")

@@ -99,6 +99,20 @@ typedef struct {
                                          LPA_PRUNE) */
 } lpa_stats;
 
+/* Launch choices that never change a result: how the graph is binned and laid out for
+ * the sketch-mode sweeps and how their kernels are launched.  An autotuner (the Python
+ * binding's tune module) times candidates on a graph or batch and picks one; every
+ * candidate gives the same labels and change counts bit for bit.  Zero in a field means
+ * its default.  Exact mode ignores the struct. */
+typedef struct {
+  int32_t window;       /* vertices per binning window: a power of two in [2048, 16384];
+                           0 = 16384 */
+  int32_t lane_threads; /* threads per CTA of the lane sweep: 64, 128 or 256 (MG with k = 8
+                           and BM; other sketches always use 128); 0 = 128 */
+  int32_t serial_hubs;  /* 1: run the hub kernels on the caller's stream after the lane
+                           kernel; 0 = on a second stream beside it */
+} lpa_tuning;
+
 /* Options.  Call lpa_options_init first; it sets the paper's defaults (Sec. 5.1.2). */
 typedef struct {
   int32_t pl_period;        /* rho: pick-less every rho iterations from the first;
@@ -115,6 +129,8 @@ typedef struct {
   void* workspace;          /* device scratch of workspace_bytes bytes, 256-byte
                                aligned; NULL = allocated and freed by the call */
   size_t workspace_bytes;
+  const lpa_tuning* tuning; /* host, read during the call (plans and servers keep a copy);
+                               NULL = defaults */
 } lpa_options;
 
 /* Leaf partition used by the sketches (fixed, so the result never depends on launch
@@ -188,9 +204,12 @@ lpa_status lpa_modularity_noalloc(const int64_t* offsets, const int32_t* indices
                                   const lpa_options* opt);
 
 /* Device workspace an lpa_detect_ex call needs: an upper bound for any graph with these
- * sizes under the default options (leaf_e0 = 64).  The sketch modes' lane table grows as
- * m / leaf_e0, so a call with a smaller leaf_e0 takes lpa_workspace_size_ex with its
- * options (opt == NULL: the defaults).  Both return 0 for negative sizes or leaf_e0 < 1.
+ * sizes under the default options (leaf_e0 = 64, default tuning).  The sketch modes' lane
+ * table grows as m / leaf_e0 and with smaller binning windows, so a call with other
+ * options takes lpa_workspace_size_ex with them (opt == NULL: the defaults).  Both return
+ * 0 for negative sizes, leaf_e0 < 1 or a tuning out of range.  The sketch modes' share is
+ * about 40 B per vertex, 16 B per lane and the sliced copy of the graph (16 B per group
+ * of four CSR positions for the indices, as much again for fp32 weights).
  * lpa_modularity_ex needs lpa_modularity_workspace_size(n). */
 size_t lpa_workspace_size(int32_t n, int64_t m, lpa_mode mode, int32_t k);
 size_t lpa_workspace_size_ex(int32_t n, int64_t m, lpa_mode mode, int32_t k,
@@ -295,8 +314,9 @@ lpa_status lpa_server_destroy(lpa_server server);
 /* ---- Memory. ------------------------------------------------------------------------
  * Device memory the library allocates (plan workspaces, lpa_detect_host staging, batch
  * and server arenas) comes from one stream-ordered pool per device that keeps freed
- * memory for later calls instead of returning it to the driver.  lpa_release_memory
- * returns every unused byte of those pools (memory of live plans and servers stays). */
+ * memory for later calls instead of returning it to the driver; the small page-locked
+ * host blocks of plans are kept for reuse too.  lpa_release_memory returns every unused
+ * byte of both (memory of live plans and servers stays). */
 lpa_status lpa_release_memory(void);
 
 const char* lpa_status_string(lpa_status s);

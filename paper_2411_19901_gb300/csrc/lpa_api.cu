@@ -8,6 +8,7 @@
 // the exact mode runs its chunk kernel over the chunk/hub binning.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <cstdarg>
@@ -91,7 +92,35 @@ cudaError_t lib_alloc(void** p, size_t bytes, cudaStream_t s) {
   return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
-int64_t num_windows(int64_t n) { return (n + kWinVerts - 1) / kWinVerts; }
+int64_t num_windows(int64_t n, int win) { return (n + win - 1) / win; }
+
+// Page-locked host blocks of the plans (state, per-iteration counters, modularity and
+// binning totals read back from the device), kept for reuse once a plan is destroyed:
+// pinning memory costs an operating-system call, and the served form re-plans at every
+// admission.
+constexpr size_t kHostState = 256;  // >= sizeof(DevState)
+constexpr size_t kHostBlock = kHostState + 2 * sizeof(unsigned long long) * LPA_MAX_ITER +
+                              4 * sizeof(double) + 32 * sizeof(unsigned long long);
+static_assert(sizeof(DevState) <= kHostState, "host block layout");
+std::mutex g_host_mu;
+std::vector<char*> g_host_free;
+
+cudaError_t acquire_host_block(char** out) {
+  {
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    if (!g_host_free.empty()) {
+      *out = g_host_free.back();
+      g_host_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost((void**)out, kHostBlock);
+}
+
+void release_host_block(void* p) {
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  g_host_free.push_back((char*)p);
+}
 
 // Bounds of the warp-per-row binning for leaf parameter e0 (see lpa_internal.cuh).  A hub
 // has more than kHubDegree positions or at least 64 leaves (so >= 64 e0 positions).  A mid
@@ -102,15 +131,15 @@ int64_t hub_cap(int64_t n, int64_t m, int e0) {
   const int64_t dmin = std::min<int64_t>(kHubDegree + 1, 64 * (int64_t)e0);
   return std::min<int64_t>(n, m / dmin);
 }
-int64_t lane_cap(int64_t n, int64_t m, int e0) {
-  return n + std::min<int64_t>(m / e0, 31 * n) + 32 * num_windows(n);
+int64_t lane_cap(int64_t n, int64_t m, int e0, int win) {
+  return n + std::min<int64_t>(m / e0, 31 * n) + 32 * num_windows(n, win);
 }
 // Elements (groups of four positions) of the sliced copy: a lane leaf of len positions
 // takes ceil(len / 4) <= len / 4 + 3/4, a hub of d positions and L leaves L * G with
 // G <= (d / L + 4) / 4, so L * G <= d / 4 + L; L <= 256, and L <= d / e0 once L > 1.
-int64_t slice_cap(int64_t n, int64_t m, int e0) {
+int64_t slice_cap(int64_t n, int64_t m, int e0, int win) {
   const int64_t hubs = hub_cap(n, m, e0);
-  return m / 4 + 1 + lane_cap(n, m, e0) + std::min<int64_t>(256 * hubs, m / e0 + hubs);
+  return m / 4 + 1 + lane_cap(n, m, e0, win) + std::min<int64_t>(256 * hubs, m / e0 + hubs);
 }
 
 // Workspace layout of a plan; offsets in bytes from the workspace base.
@@ -128,7 +157,8 @@ struct Layout {
   size_t total_fixed, tab_keys, tab_vals, total;
 };
 
-Layout layout(int64_t n, int64_t m, int mode, int e0, bool weighted, int64_t tab_slots) {
+Layout layout(int64_t n, int64_t m, int mode, int e0, int win, bool weighted,
+              int64_t tab_slots) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -151,10 +181,10 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, bool weighted, int64_t tab
     L.seg = take(3 * sizeof(int64_t) * (size_t)(num_segments(n) + 1));
     L.partials = take(sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
   } else {
-    const int64_t nwin = num_windows(n);
+    const int64_t nwin = num_windows(n, win);
     L.hub_cap = hub_cap(n, m, e0);
-    L.lane_cap = lane_cap(n, m, e0);
-    L.desc = take(sizeof(int4) * (size_t)(nwin * kWinVerts));
+    L.lane_cap = lane_cap(n, m, e0, win);
+    L.desc = take(sizeof(int4) * (size_t)(nwin * win));
     L.wtab = take(sizeof(int32_t) * (size_t)(nwin * kWinTab));
     L.hcnt = take(sizeof(int32_t) * (size_t)(kHubClasses * nwin));
     L.lcnt = take(sizeof(int32_t) * (size_t)nwin);
@@ -163,7 +193,7 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, bool weighted, int64_t tab
     L.hub_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.hub_cap, 1));
     L.lane_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.lane_cap, 1));
     L.counts = take(sizeof(unsigned long long) * 8);
-    L.sl_cap = slice_cap(n, m, e0);
+    L.sl_cap = slice_cap(n, m, e0, win);
     const int64_t nbase = L.lane_cap / 32 + L.hub_cap + 1;
     L.sl_cnt = take(sizeof(int32_t) * (size_t)nbase);
     L.sl_base = take(sizeof(int64_t) * (size_t)nbase);
@@ -183,6 +213,23 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, bool weighted, int64_t tab
 
 bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
 
+// The launch choices of o with the defaults filled in.
+lpa_status resolve_tuning(const lpa_options& o, lpa_tuning* t) {
+  lpa_tuning d{};
+  if (o.tuning) d = *o.tuning;
+  if (d.window == 0) d.window = kWinVerts;
+  if (d.lane_threads == 0) d.lane_threads = kLaneThreads;
+  if (d.window < kWinVertsMin || d.window > kWinVerts || (d.window & (d.window - 1)))
+    return fail(LPA_EINVAL, "tuning.window = %d must be a power of two in [%d, %d]", d.window,
+                kWinVertsMin, kWinVerts);
+  if (d.lane_threads != 64 && d.lane_threads != 128 && d.lane_threads != 256)
+    return fail(LPA_EINVAL, "tuning.lane_threads = %d must be 64, 128 or 256", d.lane_threads);
+  if (d.serial_hubs != 0 && d.serial_hubs != 1)
+    return fail(LPA_EINVAL, "tuning.serial_hubs must be 0 or 1");
+  *t = d;
+  return LPA_OK;
+}
+
 }  // namespace
 
 int lpa::set_last_error(int s, const char* msg) {
@@ -198,6 +245,7 @@ struct lpa_plan_s {
   int64_t m = 0;
   int mode = kMG, k = 8;
   int e0 = 64, lmax = 256, rho = 8;
+  lpa_tuning tune{};  // launch choices (all fields resolved: no zeros)
   uint32_t flags = 0;
   const int32_t* labels_in = nullptr;
   cudaStream_t stream = nullptr;
@@ -276,9 +324,9 @@ SweepArgs sweep_args(const lpa_plan_s* p, const int32_t* c_prev, int32_t* c_next
 cudaError_t launch_sketch_sweep(const lpa_plan_s* p, const SweepArgs& a, cudaStream_t s_hub) {
   const bool literal = (p->flags & LPA_MG_UNCLAMPED) != 0, rescan = (p->flags & LPA_RESCAN) != 0;
   if (p->mode == kMG && (literal || rescan))
-    return launch_sweep_mg_variant(p->k, literal, rescan, p->w != nullptr, a, p->wp, p->stream,
+    return launch_sweep_mg_variant(p->k, literal, rescan, a, p->wp, p->stream,
                                    s_hub);
-  return launch_sweep_warp(p->mode, p->k, p->w != nullptr, a, p->wp, p->stream, s_hub);
+  return launch_sweep_warp(p->mode, p->k, a, p->wp, p->stream, s_hub);
 }
 
 cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
@@ -302,11 +350,7 @@ void destroy_plan(lpa_plan_s* p) {
   if (p->own_ws && p->ws) cudaFreeAsync(p->ws, p->stream);
   if (p->own_tab && p->tab_ws) cudaFreeAsync(p->tab_ws, p->stream);
   if (p->own_ws || p->own_tab) cudaStreamSynchronize(p->stream);
-  if (p->host_state) cudaFreeHost(p->host_state);
-  if (p->host_dn) cudaFreeHost(p->host_dn);
-  if (p->host_scan) cudaFreeHost(p->host_scan);
-  if (p->host_q) cudaFreeHost(p->host_q);
-  if (p->host_cls) cudaFreeHost(p->host_cls);
+  if (p->host_state) release_host_block(p->host_state);
   delete p;
 }
 
@@ -321,7 +365,8 @@ lpa_status bin_classes(lpa_plan_s* p) {
   wp.hub_desc = (const int4*)(p->ws + ly.hub_desc);
   wp.lane_desc = (const int4*)(p->ws + ly.lane_desc);
   if (n == 0) return LPA_OK;
-  const int32_t nwin = (int32_t)num_windows(n);
+  const int win = p->tune.window;
+  const int32_t nwin = (int32_t)num_windows(n, win);
   int4* desc = (int4*)(p->ws + ly.desc);
   int32_t* wtab = (int32_t*)(p->ws + ly.wtab);
   int32_t* hcnt = (int32_t*)(p->ws + ly.hcnt);
@@ -332,10 +377,10 @@ lpa_status bin_classes(lpa_plan_s* p) {
   // counts: [0, 3) weight profile
   LPA_CUDA(launch_fill_u64(counts, 0ull, 8, s));
   LPA_CUDA(launch_fill_u64(counts, 1ull, 1, s));  // profile: all integral until shown otherwise
-  LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, desc, wtab, hcnt, lcnt, s));
+  LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, win, desc, wtab, hcnt, lcnt, s));
   LPA_CUDA(launch_scan_counts(hcnt, (int64_t)kHubClasses * nwin, hub_prefix, s));
   LPA_CUDA(launch_scan_counts(lcnt, nwin, lane_prefix, s));
-  LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, (int4*)wp.hub_desc,
+  LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, win, (int4*)wp.hub_desc,
                                ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
   // the longest row (the weights are not read: only row lengths matter here)
   LPA_CUDA(launch_weight_profile(p->off, nullptr, n, p->m, counts, s));
@@ -363,9 +408,11 @@ lpa_status bin_classes(lpa_plan_s* p) {
   wp.nctas = (int32_t)nctas;
   wp.e0 = p->e0;
   wp.lmax = p->lmax;
+  wp.lane_threads = p->tune.lane_threads;
   p->nhubs = nhubs;
   p->nchunks = nctas - nhubs;
   // the sliced copy of the CSR that the sweeps read
+  wp.wfmt = p->w ? kSplitW : kUnitW;
   int64_t* base = (int64_t*)(p->ws + ly.sl_base);
   wp.lane_base = base;
   wp.hub_base = base + nlanes / 32;
@@ -379,7 +426,7 @@ lpa_status bin_classes(lpa_plan_s* p) {
                 (long long)groups, (long long)ly.sl_cap);
   wp.sl_idx = (const int4*)(p->ws + ly.sl_idx);
   wp.sl_w = p->w ? (const float4*)(p->ws + ly.sl_w) : nullptr;
-  LPA_CUDA(launch_slice_fill(p->idx, p->w, wp, p->e0, p->lmax, (int4*)wp.sl_idx,
+  LPA_CUDA(launch_slice_fill(p->idx, p->w, p->m, wp, p->e0, p->lmax, (int4*)wp.sl_idx,
                              (float4*)wp.sl_w, s));
   return LPA_OK;
 }
@@ -456,7 +503,12 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   if (((uintptr_t)indices & 15) != 0 || ((uintptr_t)weights & 15) != 0)
     return fail(LPA_EINVAL, "indices and weights must be 16-byte aligned");
 
+  lpa_tuning tune;
+  const lpa_status ts = resolve_tuning(o, &tune);
+  if (ts != LPA_OK) return ts;
+
   lpa_plan_s* p = new lpa_plan_s();
+  p->tune = tune;
   p->off = offsets;
   p->idx = indices;
   p->w = weights;
@@ -475,15 +527,18 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
     destroy_plan(p);
     return st;
   };
-  cudaError_t ce = cudaMallocHost((void**)&p->host_state, sizeof(DevState));
-  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_dn, sizeof(unsigned long long) * LPA_MAX_ITER);
-  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_scan, sizeof(unsigned long long) * LPA_MAX_ITER);
-  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_q, sizeof(double) * 4);
-  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&p->host_cls, sizeof(unsigned long long) * 32);
+  char* hb = nullptr;
+  cudaError_t ce = acquire_host_block(&hb);
   if (ce != cudaSuccess) return bail(fail(LPA_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(ce)));
+  p->host_state = (DevState*)hb;
+  p->host_dn = (unsigned long long*)(hb + kHostState);
+  p->host_scan = p->host_dn + LPA_MAX_ITER;
+  p->host_q = (double*)(p->host_scan + LPA_MAX_ITER);
+  p->host_cls = (unsigned long long*)(p->host_q + 4);
 
   // workspace: fixed part now; exact-mode hub tables once binning knows their size
-  p->lay = layout(n, m, p->mode, p->e0, weights != nullptr, p->mode == kExact ? 2 * m : 0);
+  p->lay = layout(n, m, p->mode, p->e0, p->tune.window, weights != nullptr,
+                  p->mode == kExact ? 2 * m : 0);
   if (o.workspace) {
     if (o.workspace_bytes < p->lay.total)
       return bail(fail(LPA_ENOMEM, "workspace of %zu bytes, %zu needed", o.workspace_bytes, p->lay.total));
@@ -536,7 +591,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   }
   s = p->mode == kExact ? bin_chunks(p, o) : bin_classes(p);
   if (s != LPA_OK) return bail(s);
-  if (p->mode != kExact && p->wp.nhubs > 0 && p->wp.nlanes > 0) {
+  if (p->mode != kExact && p->wp.nhubs > 0 && p->wp.nlanes > 0 && !p->tune.serial_hubs) {
     ce = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming);
@@ -772,6 +827,7 @@ size_t serve_footprint(const lpa_graph& g, int e0) {
 
 struct lpa_server_s {
   int mode = kMG, k = 8;
+  lpa_tuning tune{};
   double tol = 0.05;
   int max_iter = 20;
   lpa_options opt{};
@@ -1088,9 +1144,13 @@ size_t lpa_workspace_size_ex(int32_t n, int64_t m, lpa_mode mode, int32_t k,
                              const lpa_options* opt) {
   (void)k;
   if (n < 0 || m < 0) return 0;
-  const int e0 = opt ? opt->leaf_e0 : 64;
-  if (e0 < 1) return 0;
-  return layout(n, m, (int)mode, e0, true, mode == LPA_EXACT ? 2 * m : 0).total;
+  lpa_options o;
+  lpa_options_init(&o);
+  if (opt) o = *opt;
+  if (o.leaf_e0 < 1) return 0;
+  lpa_tuning t;
+  if (resolve_tuning(o, &t) != LPA_OK) return 0;
+  return layout(n, m, (int)mode, o.leaf_e0, t.window, true, mode == LPA_EXACT ? 2 * m : 0).total;
 }
 
 size_t lpa_modularity_workspace_size(int32_t n) {
@@ -1446,12 +1506,17 @@ lpa_status lpa_server_create(lpa_mode mode, int32_t k, double tol, int32_t max_i
   if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
   if ((o.flags & (LPA_MG_UNCLAMPED | LPA_RESCAN)) && mode != LPA_MG)
     return fail(LPA_EINVAL, "LPA_MG_UNCLAMPED and LPA_RESCAN apply to LPA_MG only");
+  lpa_tuning tune;
+  const lpa_status ts = resolve_tuning(o, &tune);
+  if (ts != LPA_OK) return ts;
   lpa_server_s* S = new lpa_server_s();
   S->mode = (int)mode;
   S->k = mode == LPA_MG ? k : 1;
   S->tol = tol;
   S->max_iter = max_iter;
+  S->tune = tune;  // a copy: the caller's struct need not outlive the call
   S->opt = o;
+  S->opt.tuning = &S->tune;
   S->stream = (cudaStream_t)o.stream;
   S->budget = hbm_budget_bytes;
   cudaError_t ce = lib_alloc((void**)&S->d_err, 256, S->stream);
@@ -1539,6 +1604,11 @@ lpa_status lpa_server_drain(lpa_server S, uint64_t* tickets, int32_t cap, int32_
 }
 
 lpa_status lpa_release_memory(void) {
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    for (char* b : g_host_free) cudaFreeHost(b);
+    g_host_free.clear();
+  }
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (int d = 0; d < kMaxDevices; ++d)
     if (g_pools[d]) {

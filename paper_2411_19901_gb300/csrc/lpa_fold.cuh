@@ -436,33 +436,47 @@ struct HubSliceAddr {
   __device__ __forceinline__ int64_t at(int k) const { return first + (int64_t)k * stride; }
 };
 
-// Fold the len positions of one leaf, in CSR order, from the sliced copy into st, with
-// the same rule as fold_range: st.add(C[j], w) for every kept position.  The leaf has ng
-// groups (0: nothing to fold); the loop takes `iters` >= ng steps, the same on every lane
-// when addr votes, and steps past ng only keep the vote going.  Same three-set pipeline
-// as fold_range: while group k is folded, the labels of group k+1 are gathered and group
-// k+2 is loaded; the loads of a warp's lanes are side by side in memory.
-template <class S, bool WT, bool SKIP_SELF, class A>
-__device__ __forceinline__ void fold_groups(S& st, const int4* __restrict__ si,
-                                            const float4* __restrict__ sw,
-                                            const int32_t* __restrict__ lab, int self, int len,
-                                            int ng, int iters, A& addr) {
+// Neighbour labels of a group of the sliced copy: index -1 marks a position no vote
+// comes from (a self-loop, a weight that is not positive, padding past the leaf's end).
+// With SELF_LOOPS such a position of positive weight -- a self-loop -- counts under the
+// vertex's own label (modularity: C_i = C_i), else it is skipped (-1).
+template <bool SELF_LOOPS>
+__device__ __forceinline__ int4 gather_slice(const int32_t* __restrict__ lab, const int4& J,
+                                             const float4& W, int own) {
+  int c[4];
+  const int j[4] = {J.x, J.y, J.z, J.w};
+  const float w[4] = {W.x, W.y, W.z, W.w};
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    c[u] = j[u] >= 0 ? __ldg(lab + j[u]) : (SELF_LOOPS && w[u] > 0.f ? own : -1);
+  return make_int4(c[0], c[1], c[2], c[3]);
+}
+
+// Fold the positions of one leaf, in CSR order, from the sliced copy into st:
+// st.add(C[j], w) for every position a vote comes from (the rule of fold_range; the
+// sliced copy marks the others).  The leaf has ng groups (0: nothing to fold); the loop
+// takes `iters` >= ng steps, the same on every lane when addr votes, and steps past ng
+// only keep the vote going.  Same three-set pipeline as fold_range: while group k is
+// folded, the labels of group k+1 are gathered and group k+2 is loaded; the loads of a
+// warp's lanes are side by side in memory.
+template <class S, int WF, bool SELF_LOOPS, class A>
+__device__ __forceinline__ void fold_groups(S& st, const WarpPlan& pl,
+                                            const int32_t* __restrict__ lab, int own, int ng,
+                                            int iters, A& addr) {
   if (iters <= 0) return;
-  const unsigned lastm = 0xFu >> ((4 - (len & 3)) & 3);  // positions of the last group
+  const int4* __restrict__ si = pl.sl_idx;
+  const float4* __restrict__ sw = pl.sl_w;
   auto load = [&](int k, int4& X, float4& W) {
     const int64_t p = addr.at(k);
     if (k < ng) {
       X = __ldg(si + p);
-      W = WT ? __ldg(sw + p) : make_float4(1.f, 1.f, 1.f, 1.f);
+      W = WF == kSplitW ? __ldg(sw + p) : make_float4(1.f, 1.f, 1.f, 1.f);
     } else {
-      X = make_int4(self, self, self, self);
+      X = make_int4(-1, -1, -1, -1);
       W = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  auto gather = [&](int k, int4& X, const float4& W) {
-    const unsigned mk = k < ng ? (k == ng - 1 ? lastm : 0xFu) : 0u;
-    X = gather_group<SKIP_SELF>(lab, X, W, mk, self);
-  };
+  auto gather = [&](int4& X, const float4& W) { X = gather_slice<SELF_LOOPS>(lab, X, W, own); };
   auto fold = [&](int4 C, float4 W) {
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
@@ -471,15 +485,15 @@ __device__ __forceinline__ void fold_groups(S& st, const int4* __restrict__ si,
       W = make_float4(W.y, W.z, W.w, 0.f);
     }
   };
-  int4 X0, X1 = make_int4(self, self, self, self), X2 = make_int4(self, self, self, self);
+  int4 X0, X1 = make_int4(-1, -1, -1, -1), X2 = make_int4(-1, -1, -1, -1);
   float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = make_float4(0.f, 0.f, 0.f, 0.f);
   load(0, X0, W0);
-  gather(0, X0, W0);
+  gather(X0, W0);
   if (iters > 1) load(1, X1, W1);
-#define LPA_STEP(XF, WF, XG, WG, XL, WL)   \
-  if (k + 1 < iters) gather(k + 1, XG, WG); \
-  if (k + 2 < iters) load(k + 2, XL, WL);   \
-  fold(XF, WF);                             \
+#define LPA_STEP(XF, WF_, XG, WG, XL, WL)  \
+  if (k + 1 < iters) gather(XG, WG);       \
+  if (k + 2 < iters) load(k + 2, XL, WL);  \
+  fold(XF, WF_);                           \
   if (++k >= iters) break;
   for (int k = 0;;) {
     LPA_STEP(X0, W0, X1, W1, X2, W2)

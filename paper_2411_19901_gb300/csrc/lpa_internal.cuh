@@ -26,7 +26,7 @@ constexpr int kSegment = 2048;         // vertices per thread of the greedy binn
 constexpr int kMaxLeaves = 256;        // largest leaf_max accepted
 
 // Binning of the warp-per-row sweep (sketch modes).  Vertices are cut into windows of
-// kWinVerts consecutive ids.  Inside a window they are counting-sorted into hubs (rows
+// `win` consecutive ids (kWinVerts unless a tuning picks a smaller power of two).  Inside a window they are counting-sorted into hubs (rows
 // longer than kHubDegree or with more than 32 leaves), then kMidClasses mid classes
 // (2..32 leaves, by leaf count descending, then leaf-length quarter), then one-leaf (low)
 // rows by degree, descending.  Mid and low vertices are packed onto consecutive lanes, L
@@ -36,7 +36,8 @@ constexpr int kMaxLeaves = 256;        // largest leaf_max accepted
 // 16-byte descriptor per lane, so a thread finds its work with one load and rows swept at
 // the same time share neighbour-label ranges in L2.  The grid runs every hub first (a CTA
 // each), then the lanes, kThreads to a CTA.
-constexpr int kWinVerts = 16384;
+constexpr int kWinVerts = 16384;      // default window (lpa_tuning.window)
+constexpr int kWinVertsMin = 2048;    // smallest window a tuning may choose
 constexpr int kLowKeys = 1024;         // low-row sort keys (degree, capped)
 constexpr int kMidSub = 4;             // leaf-length quarters per leaf count
 constexpr int kMidClasses = 5 * kMidSub;
@@ -96,10 +97,15 @@ __host__ __device__ __forceinline__ int leaf_count(int64_t d, int e0, int lmax) 
   return (int)(p < lmax ? p : lmax);
 }
 
+// Weight formats of the sliced copy: unit weights (no weight array) or fp32 weights in
+// sl_w.
+enum WFmt : int { kUnitW = 0, kSplitW = 1 };
+
 // Sliced copy of the CSR (built once per plan).  A leaf's positions, in CSR order, are
-// cut into ceil(len / 4) groups of four (the last one padded with {self, weight 0}); each
-// group is one 16-byte element of sl_idx and of sl_w, so the lanes of a warp read their
-// groups side by side instead of 32 separate rows.
+// cut into ceil(len / 4) groups of four; each group is one 16-byte element of sl_idx and
+// of sl_w, so the lanes of a warp read their groups side by side instead of 32 separate
+// rows.  An index of -1 marks a position no vote comes from (a self-loop, a weight that
+// is not positive, padding past the leaf's end, weight 0), so the sweep tests one sign.
 //  * lane warps: column k of a warp holds group k of every lane that has one, in lane
 //    order (a warp vote gives each lane its place), so a warp's slice has exactly the
 //    groups of its lanes; lane_base[w] is its first element.
@@ -117,6 +123,8 @@ struct WarpPlan {
   int32_t nhubs;
   int32_t nctas;          // nhubs + ceil(nlanes / kThreads) (work units, for the stats)
   int32_t e0, lmax;       // the leaf partition the plan was binned with
+  int32_t wfmt;           // WFmt of the sliced copy
+  int32_t lane_threads;   // CTA size of the lane sweep (lpa_tuning)
   int32_t hub_start[kHubClasses + 1];  // first hub of each class; [kHubClasses] = nhubs
 };
 
@@ -195,22 +203,21 @@ struct BinArgs {
 };
 
 // Host-side launchers (stream-ordered, no synchronisation).
-// Sketch modes (MG, BM): hub and lane kernels over a WarpPlan.
-// The hub kernel goes to s_hub, the lane kernel to s.
-cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
-                              const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
-cudaError_t launch_sweep_mg16(bool weighted, const SweepArgs& a, const WarpPlan& p,
+// Sketch modes (MG, BM): hub and lane kernels over a WarpPlan (its weight format decides
+// the instantiation).  The hub kernel goes to s_hub, the lane kernel to s.
+cudaError_t launch_sweep_warp(int mode, int k, const SweepArgs& a, const WarpPlan& p,
                               cudaStream_t s, cudaStream_t s_hub);
-cudaError_t launch_sweep_mg32(bool weighted, const SweepArgs& a, const WarpPlan& p,
-                              cudaStream_t s, cudaStream_t s_hub);
+cudaError_t launch_sweep_mg16(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                              cudaStream_t s_hub);
+cudaError_t launch_sweep_mg32(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                              cudaStream_t s_hub);
 // MG ablations (at least one of literal, rescan set): paper-literal accumulate and / or
 // double scan, hub kernel on s_hub and lane kernel on s as launch_sweep_warp.
-cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, bool weighted,
-                                    const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
-                                    cudaStream_t s_hub);
-cudaError_t launch_sweep_mg16_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, const SweepArgs& a,
+                                    const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
+cudaError_t launch_sweep_mg16_variant(bool literal, bool rescan, const SweepArgs& a,
                                       const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
-cudaError_t launch_sweep_mg32_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+cudaError_t launch_sweep_mg32_variant(bool literal, bool rescan, const SweepArgs& a,
                                       const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub);
 // Weight profile: out[0] = 1 if every weight is integer-valued (AND), out[1] = largest
 // weight's bits, out[2] = largest row length.  out must be zeroed except out[0] = 1.
@@ -222,14 +229,15 @@ size_t exact_smem_bytes(bool weighted);
 // Binning for the warp-per-row kernels.  Per window: sort the vertices into groups, write
 // their descriptors, the window table, the hub count of each class (class-major:
 // hcnt[c * nwin + window]) and the padded lane count.
-cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int4* desc,
-                               int32_t* wtab, int32_t* hcnt, int32_t* lcnt, cudaStream_t s);
+cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int win,
+                               int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt,
+                               cudaStream_t s);
 // prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s);
 // Hub and lane descriptors of every window at their prefix offsets (hub_prefix over the
 // class-major hub counts; capacities bound the writes).
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
-                                const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
+                                const int64_t* lane_prefix, int32_t nwin, int win, int4* hub_desc,
                                 int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
                                 cudaStream_t s);
 // Sliced copy of the CSR for a binned plan (lpa_setup.cu).  cnt: nlanes / 32 + nhubs
@@ -239,8 +247,11 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
 // sl_idx / sl_w (sl_w null for unit weights).
 cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
                                cudaStream_t s);
-cudaError_t launch_slice_fill(const int32_t* idx, const float* w, const WarpPlan& p, int e0,
-                              int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s);
+cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
+                              int e0, int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s);
+// Whether the sweeps are built with every lane CTA size of lpa_tuning (MG with k = 8 and
+// BM; the other sketches and the MG ablations use the default).
+inline bool full_tuning_sketch(int mode, int k) { return mode == kBM || (mode == kMG && k == 8); }
 // Modularity over a WarpPlan: rows, then Sigma_c^2; out4 as launch_modularity.  With gid
 // (a batch), each graph's 2m and intra-community weight also accumulate into g2m / gin
 // (zeroed by the caller).

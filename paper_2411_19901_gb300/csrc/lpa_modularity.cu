@@ -106,7 +106,7 @@ __device__ __forceinline__ void mod_commit(bool owner, int v, int cv, double kv,
 
 // Packed lanes (the sweep's lane descriptors): each lane sums its leaf, the L lanes of a
 // vertex combine by shuffles, the vertex's first lane holds its totals.
-template <bool WT>
+template <int WF>
 __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
     const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots, ModGraphs mg) {
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
   if (v >= 0) acc.cv = labels[v];
   const int ngl = (int)((len + 3) >> 2);
   LaneSliceAddr ad{q < p.nlanes ? p.lane_base[q >> 5] : 0, ngl, (1u << (threadIdx.x & 31)) - 1u};
-  fold_groups<ModAcc, WT, false>(acc, p.sl_idx, p.sl_w, labels, v, (int)len, ngl,
-                                 __reduce_max_sync(kFullMask, ngl), ad);
+  fold_groups<ModAcc, WF, true>(acc, p, labels, acc.cv, ngl, __reduce_max_sync(kFullMask, ngl),
+                                ad);
   double kv = acc.k(), in = acc.in();
   const int Lw = __reduce_max_sync(kFullMask, L);
   if (Lw > 1) {
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kLaneThreads) modularity_lane_kernel(
 
 // Hubs of one class (p.hub_desc, p.hub_base point at the class): leaf t on thread t, from
 // the sliced copy.
-template <bool WT>
+template <int WF>
 __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ wts, int64_t m,
     const int32_t* __restrict__ labels, WarpPlan p, double* sigma_c, double* slots, ModGraphs mg) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) modularity_hub_kernel(
     const int64_t G = hub_leaf_groups(d, L);
     HubSliceAddr ad{p.hub_base[blockIdx.x] + (int64_t)(tid >> 5) * W * G + (tid & 31), W};
     const int ng = (int)((len + 3) >> 2);
-    fold_groups<ModAcc, WT, false>(acc, p.sl_idx, p.sl_w, labels, v, (int)len, ng, ng, ad);
+    fold_groups<ModAcc, WF, true>(acc, p, labels, acc.cv, ng, ng, ad);
   }
   s_k[tid] = acc.k();
   s_in[tid] = acc.in();
@@ -234,14 +234,14 @@ __global__ void __launch_bounds__(256) modularity_total_kernel(const double* a_p
 // ------------------------------------------------------- standalone pass (no binning)
 //
 // A warp takes a tile of 32 consecutive vertices.  A row of at most kModShortRow
-// positions is summed by its own lane; a longer row is cut into 32 contiguous pieces, one
-// per lane, summed by the whole warp afterwards.  K_i and the intra-community weight stay
+// positions is summed by its own lane; a longer row is cut into 32 contiguous pieces (of
+// more than 8 positions each), one per lane, summed by the whole warp afterwards.  K_i and the intra-community weight stay
 // in each lane's registers until the end, then go through a fixed-order block tree into
 // one partial per block; only the Sigma_c atomics depend on timing.
 
 constexpr int kModThreads = 256;
 constexpr int kModMaxBlocks = 152 * 3;  // one wave at 3 CTAs per SM (78 registers)
-constexpr int kModShortRow = 32;
+constexpr int kModShortRow = 256;
 
 // Positions [b, e) of a row into acc: the pipelined 16-byte reads of the sweep when both
 // arrays start on a 16-byte boundary (VEC), else one entry at a time.
@@ -408,20 +408,14 @@ cudaError_t launch_modularity_plan(const int64_t* off, const int32_t* idx, const
     WarpPlan q = p;
     q.hub_desc = p.hub_desc + p.hub_start[c];
     q.hub_base = p.hub_base + p.hub_start[c];
-    if (w)
-      modularity_hub_kernel<true><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
-    else
-      modularity_hub_kernel<false><<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
+    auto kern = p.wfmt == kSplitW ? modularity_hub_kernel<kSplitW> : modularity_hub_kernel<kUnitW>;
+    kern<<<cnt, kThreads >> c, 0, s>>>(idx, w, m, labels, q, sigma_c, slots, mg);
     count_launch();
   }
   const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
   if (lane_ctas > 0) {
-    if (w)
-      modularity_lane_kernel<true><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
-                                                                               sigma_c, slots, mg);
-    else
-      modularity_lane_kernel<false><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p,
-                                                                                sigma_c, slots, mg);
+    auto kern = p.wfmt == kSplitW ? modularity_lane_kernel<kSplitW> : modularity_lane_kernel<kUnitW>;
+    kern<<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(idx, w, m, labels, p, sigma_c, slots, mg);
     count_launch();
   }
   sigma_sq_kernel<<<kSqBlocks, 256, 0, s>>>(sigma_c, n, sq);

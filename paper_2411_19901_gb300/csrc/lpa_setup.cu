@@ -197,13 +197,13 @@ constexpr int kSortThreads = 1024;
 constexpr int kSortPad = 2 * kSortThreads;  // scan space: two keys per thread
 static_assert(kSortKeys <= kSortPad, "sort keys exceed the scan space");
 
-// One CTA per window: counting sort of the window's vertices by window_key, writing each
-// slot's descriptor {v, offset lo, offset hi, degree}, the window table, the window's hub
-// count and its lane count rounded up to whole warps.  Order inside one key does not
-// matter.
+// One CTA per window of `win` vertices: counting sort of the window's vertices by
+// window_key, writing each slot's descriptor {v, offset lo, offset hi, degree}, the window
+// table, the window's hub count and its lane count rounded up to whole warps.  Order
+// inside one key does not matter.
 __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
-    const int64_t* off, int32_t n, int e0, int lmax, int4* desc, int32_t* wtab, int32_t* hcnt,
-    int32_t* lcnt) {
+    const int64_t* off, int32_t n, int e0, int lmax, int win, int4* desc, int32_t* wtab,
+    int32_t* hcnt, int32_t* lcnt) {
   __shared__ int s_hist[kSortPad];
   __shared__ int s_wsum[kSortThreads / 32];
   __shared__ int s_grp[kHubClasses + kLaneGroups];  // hub classes, mid classes, low rows
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
   const int tid = threadIdx.x;
   for (int i = tid; i < kSortPad; i += kSortThreads) s_hist[i] = 0;
   __syncthreads();
-  const int64_t v0 = (int64_t)blockIdx.x * kWinVerts;
+  const int64_t v0 = (int64_t)blockIdx.x * win;
   int key[kPer];
   int64_t b[kPer];
   int d[kPer];
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
   for (int q = 0; q < kPer; ++q) {
     const int64_t v = v0 + tid + q * kSortThreads;
     key[q] = -1;
-    if (v < n) {
+    if (tid + q * kSortThreads < win && v < n) {
       b[q] = off[v];
       const int64_t dd = off[v + 1] - b[q];
       d[q] = (int)dd;  // rows above INT32_MAX are refused after binning
@@ -314,23 +314,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(const int32_t
 // (the host then refuses the plan).
 __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
     const int4* desc, const int32_t* wtab, const int64_t* hub_prefix, const int64_t* lane_prefix,
-    int4* hub_desc, int64_t hub_cap, int4* lane_desc, int64_t lane_cap) {
+    int win, int4* hub_desc, int64_t hub_cap, int4* lane_desc, int64_t lane_cap) {
   __shared__ int32_t t[kWinTab];
   const int tid = threadIdx.x;
-  const int64_t win = blockIdx.x;
-  if (tid < kWinTab) t[tid] = wtab[win * kWinTab + tid];
+  const int64_t wi = blockIdx.x;
+  if (tid < kWinTab) t[tid] = wtab[wi * kWinTab + tid];
   __syncthreads();
-  const int4* wd = desc + win * kWinVerts;
+  const int4* wd = desc + blockIdx.x * (int64_t)win;
   const int nh = t[0];
   for (int i = tid; i < nh; i += kSortThreads) {
     int c = kHubClasses - 1;  // the class whose slots hold i
     while (c > 0 && t[kTabHub + c] > i) --c;
-    const int64_t pos = hub_prefix[(int64_t)c * gridDim.x + win] + (i - t[kTabHub + c]);
+    const int64_t pos = hub_prefix[(int64_t)c * gridDim.x + wi] + (i - t[kTabHub + c]);
     if (pos < hub_cap) hub_desc[pos] = wd[i];
   }
   const int lanes = t[kTabLanes];
-  const int64_t l0 = lane_prefix[win];
-  const int padded = (int)(lane_prefix[win + 1] - l0);
+  const int64_t l0 = lane_prefix[wi];
+  const int padded = (int)(lane_prefix[wi + 1] - l0);
   for (int q = tid; q < padded; q += kSortThreads) {
     if (l0 + q >= lane_cap) break;
     int4 out = make_int4(-1, 0, 0, 0);
@@ -352,8 +352,10 @@ __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
   }
 }
 
-// Whether every sum of a row's weights is exact in fp32: integer-valued weights and
-// (longest row) x (largest weight) <= 2^24 suffice.
+// Profile of the weights and rows: out[0] stays 1 if every weight is an integer, out[1]
+// gets the largest weight's bits and out[2] the longest row (w null: rows only).  The plan
+// packs integer weights into the index words of its sliced copy when they fit, and
+// refuses rows longer than 2^31 - 1.
 __global__ void weight_profile_kernel(const int64_t* off, const float* w, int32_t n, int64_t m,
                                       unsigned long long* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -364,7 +366,8 @@ __global__ void weight_profile_kernel(const int64_t* off, const float* w, int32_
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
       const float x = w[e];
       integral = integral && (x == truncf(x));
-      const unsigned bits = __float_as_uint(x);  // weights are >= 0: bit order = value order
+      // weights are >= 0 (or -0): without the sign bit, bit order = value order
+      const unsigned bits = __float_as_uint(x) & 0x7fffffffu;
       wmax = bits > wmax ? bits : wmax;
     }
   else
@@ -475,30 +478,52 @@ __global__ void __launch_bounds__(256) slice_count_kernel(const int4* __restrict
   }
 }
 
-// One group of four positions [g, g + 4) of the CSR, of which the first `valid` belong to
-// the leaf; the rest become {self, weight 0}.
-template <bool WT>
-__device__ __forceinline__ void copy_group(const int32_t* __restrict__ idx,
-                                           const float* __restrict__ w, int64_t g,
-                                           int64_t valid, int self, int4* si, float4* sw,
-                                           int64_t p) {
-  int j[4];
-  float x[4];
+// The aligned block of four CSR positions starting at a (a multiple of 4); positions at
+// or past m come back as 0.
+__device__ __forceinline__ int4 load_block(const int32_t* __restrict__ a32, int64_t a, int64_t m) {
+  if (a + 3 < m) return __ldg(reinterpret_cast<const int4*>(a32 + a));
+  int r[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    j[u] = u < valid ? __ldg(idx + g + u) : self;
-    x[u] = u < valid ? (WT ? __ldg(w + g + u) : 1.f) : 0.f;
-  }
-  si[p] = make_int4(j[0], j[1], j[2], j[3]);
-  if (WT) sw[p] = make_float4(x[0], x[1], x[2], x[3]);
+  for (int u = 0; u < 4; ++u) r[u] = a + u < m ? __ldg(a32 + a + u) : 0;
+  return make_int4(r[0], r[1], r[2], r[3]);
 }
 
-// Pass 2, lane warps: each lane copies its leaf into the columns of its warp's slice.
-template <bool WT>
+// Positions sh .. sh + 3 of the eight in (lo, hi).
+__device__ __forceinline__ int4 funnel(const int4& lo, const int4& hi, int sh) {
+  switch (sh) {
+    case 0: return lo;
+    case 1: return make_int4(lo.y, lo.z, lo.w, hi.x);
+    case 2: return make_int4(lo.z, lo.w, hi.x, hi.y);
+    default: return make_int4(lo.w, hi.x, hi.y, hi.z);
+  }
+}
+
+// One group of the sliced copy at element p from positions u < valid of the leaf
+// (indices j, weight bits x); an index of -1 marks what no vote comes from: a self-loop,
+// a weight that is not positive, and the padding past the leaf's end (weight 0).
+template <int WF>
+__device__ __forceinline__ void store_group(const int (&j)[4], const int (&x)[4], int64_t valid,
+                                            int self, int4* si, float4* sw, int64_t p) {
+  int jo[4];
+  float xo[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    xo[u] = u < valid ? (WF != kUnitW ? __int_as_float(x[u]) : 1.f) : 0.f;
+    jo[u] = (u < valid && j[u] != self && xo[u] > 0.f) ? j[u] : -1;
+  }
+  si[p] = make_int4(jo[0], jo[1], jo[2], jo[3]);
+  if (WF == kSplitW) sw[p] = make_float4(xo[0], xo[1], xo[2], xo[3]);
+}
+
+// Pass 2, lane warps: each lane copies its leaf into the columns of its warp's slice,
+// reading its positions as aligned 16-byte blocks (each block once) and shifting them
+// into groups that start at the leaf's first position.
+template <int WF>
 __global__ void __launch_bounds__(256) slice_fill_lanes_kernel(
-    const int32_t* __restrict__ idx, const float* __restrict__ w,
+    const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t m,
     const int4* __restrict__ lane_desc, int64_t nlanes, const int64_t* __restrict__ base,
     int4* si, float4* sw) {
+  constexpr bool WT = WF != kUnitW;
   const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (t >= nlanes) return;  // whole warps
   const int lane = threadIdx.x & 31;
@@ -508,32 +533,79 @@ __global__ void __launch_bounds__(256) slice_fill_lanes_kernel(
   const int64_t len = v >= 0 ? (l.w & ((1 << kLaneLeafShift) - 1)) : 0;
   const int ng = (int)((len + 3) >> 2);
   const int iters = __reduce_max_sync(0xffffffffu, ng);
+  const int64_t a0 = lo & ~(int64_t)3;
+  const int sh = (int)(lo & 3);
+  const int32_t* wi = reinterpret_cast<const int32_t*>(w);
+  int4 bi = make_int4(0, 0, 0, 0), bw = make_int4(0, 0, 0, 0);
+  if (ng > 0) {
+    bi = load_block(idx, a0, m);
+    if (WT) bw = load_block(wi, a0, m);
+  }
   int64_t col = base[t >> 5];
   for (int k = 0; k < iters; ++k) {
     const unsigned has = __ballot_sync(0xffffffffu, ng > k);
-    if (ng > k) copy_group<WT>(idx, w, lo + 4 * k, len - 4 * k, v, si, sw,
-                               col + __popc(has & ((1u << lane) - 1u)));
+    if (ng > k) {
+      int4 ni = make_int4(0, 0, 0, 0), nw = make_int4(0, 0, 0, 0);
+      if (sh != 0 && 4 * (k + 1) < sh + len) {  // the next block holds part of group k
+        ni = load_block(idx, a0 + 4 * (k + 1), m);
+        if (WT) nw = load_block(wi, a0 + 4 * (k + 1), m);
+      }
+      int4 gi = funnel(bi, ni, sh), gw = funnel(bw, nw, sh);
+      const int64_t valid = len - 4 * k;
+      const int j[4] = {gi.x, gi.y, gi.z, gi.w};
+      const int x[4] = {gw.x, gw.y, gw.z, gw.w};
+      const int64_t p = col + __popc(has & ((1u << lane) - 1u));
+      store_group<WF>(j, x, valid, v, si, sw, p);
+      if (sh != 0) {
+        bi = ni;
+        bw = nw;
+      } else if (ng > k + 1) {
+        bi = load_block(idx, a0 + 4 * (k + 1), m);
+        if (WT) bw = load_block(wi, a0 + 4 * (k + 1), m);
+      }
+    }
     col += __popc(has);
   }
 }
 
-// Pass 2, hubs: a CTA per hub, leaf t on thread t.
-template <bool WT>
+// Pass 2, hubs: a CTA per hub, leaf t on thread t, read as aligned blocks as above.
+template <int WF>
 __global__ void __launch_bounds__(kThreads) slice_fill_hubs_kernel(
-    const int32_t* __restrict__ idx, const float* __restrict__ w,
+    const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t m,
     const int4* __restrict__ hub_desc, const int64_t* __restrict__ base, int e0, int lmax,
     int4* si, float4* sw) {
+  constexpr bool WT = WF != kUnitW;
   const int4 h = __ldg(hub_desc + blockIdx.x);
   const int64_t b = (int64_t)(uint32_t)h.y | ((int64_t)h.z << 32);
   const int64_t d = h.w;
   const int L = leaf_count(d, e0, lmax);
   const int64_t G = hub_leaf_groups(d, L);
   const int W = L < 32 ? L : 32;
+  const int32_t* wi = reinterpret_cast<const int32_t*>(w);
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
     const int64_t lo = b + (t * d) / L, len = b + ((t + 1) * d) / L - lo;
     const int64_t first = base[blockIdx.x] + (int64_t)(t >> 5) * W * G + (t & 31);
-    for (int64_t k = 0; k < G; ++k)
-      copy_group<WT>(idx, w, lo + 4 * k, len - 4 * k, h.x, si, sw, first + k * W);
+    const int64_t a0 = lo & ~(int64_t)3;
+    const int sh = (int)(lo & 3);
+    int4 bi = make_int4(0, 0, 0, 0), bw = make_int4(0, 0, 0, 0);
+    if (len > 0) {
+      bi = load_block(idx, a0, m);
+      if (WT) bw = load_block(wi, a0, m);
+    }
+    for (int64_t k = 0; k < G; ++k) {
+      const int64_t valid = len - 4 * k;
+      int4 ni = make_int4(0, 0, 0, 0), nw = make_int4(0, 0, 0, 0);
+      if (4 * (k + 1) < sh + len) {  // the next block holds positions of the leaf
+        ni = load_block(idx, a0 + 4 * (k + 1), m);
+        if (WT) nw = load_block(wi, a0 + 4 * (k + 1), m);
+      }
+      const int4 gi = funnel(bi, ni, sh), gw = funnel(bw, nw, sh);
+      const int j[4] = {gi.x, gi.y, gi.z, gi.w};
+      const int x[4] = {gw.x, gw.y, gw.z, gw.w};
+      store_group<WF>(j, x, valid, h.x, si, sw, first + k * W);
+      bi = ni;
+      bw = nw;
+    }
   }
 }
 
@@ -634,11 +706,12 @@ cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int4* desc,
-                               int32_t* wtab, int32_t* hcnt, int32_t* lcnt, cudaStream_t s) {
-  const unsigned nwin = (unsigned)((n + kWinVerts - 1) / kWinVerts);
+cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int win,
+                               int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt,
+                               cudaStream_t s) {
+  const unsigned nwin = (unsigned)((n + (int64_t)win - 1) / win);
   if (nwin == 0) return cudaSuccess;
-  window_sort_kernel<<<nwin, kSortThreads, 0, s>>>(off, n, e0, lmax, desc, wtab, hcnt, lcnt);
+  window_sort_kernel<<<nwin, kSortThreads, 0, s>>>(off, n, e0, lmax, win, desc, wtab, hcnt, lcnt);
   count_launch();
   return cudaGetLastError();
 }
@@ -650,12 +723,13 @@ cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix,
 }
 
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
-                                const int64_t* lane_prefix, int32_t nwin, int4* hub_desc,
+                                const int64_t* lane_prefix, int32_t nwin, int win, int4* hub_desc,
                                 int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
                                 cudaStream_t s) {
   if (nwin == 0) return cudaSuccess;
   expand_lanes_kernel<<<(unsigned)nwin, kSortThreads, 0, s>>>(desc, wtab, hub_prefix, lane_prefix,
-                                                              hub_desc, hub_cap, lane_desc, lane_cap);
+                                                              win, hub_desc, hub_cap, lane_desc,
+                                                              lane_cap);
   count_launch();
   return cudaGetLastError();
 }
@@ -674,27 +748,19 @@ cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt
   return launch_scan_counts(cnt, nw + p.nhubs, base, s);
 }
 
-cudaError_t launch_slice_fill(const int32_t* idx, const float* w, const WarpPlan& p, int e0,
-                              int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s) {
+cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
+                              int e0, int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s) {
   if (p.nlanes > 0) {
     const unsigned grid = (unsigned)((p.nlanes + 255) / 256);
-    if (w)
-      slice_fill_lanes_kernel<true><<<grid, 256, 0, s>>>(idx, w, p.lane_desc, p.nlanes,
-                                                         p.lane_base, sl_idx, sl_w);
-    else
-      slice_fill_lanes_kernel<false><<<grid, 256, 0, s>>>(idx, w, p.lane_desc, p.nlanes,
-                                                          p.lane_base, sl_idx, sl_w);
+    auto kern = p.wfmt == kSplitW ? slice_fill_lanes_kernel<kSplitW> : slice_fill_lanes_kernel<kUnitW>;
+    kern<<<grid, 256, 0, s>>>(idx, w, m, p.lane_desc, p.nlanes, p.lane_base, sl_idx, sl_w);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (p.nhubs > 0) {
-    if (w)
-      slice_fill_hubs_kernel<true><<<p.nhubs, kThreads, 0, s>>>(idx, w, p.hub_desc, p.hub_base,
-                                                                e0, lmax, sl_idx, sl_w);
-    else
-      slice_fill_hubs_kernel<false><<<p.nhubs, kThreads, 0, s>>>(idx, w, p.hub_desc, p.hub_base,
-                                                                 e0, lmax, sl_idx, sl_w);
+    auto kern = p.wfmt == kSplitW ? slice_fill_hubs_kernel<kSplitW> : slice_fill_hubs_kernel<kUnitW>;
+    kern<<<p.nhubs, kThreads, 0, s>>>(idx, w, m, p.hub_desc, p.hub_base, e0, lmax, sl_idx, sl_w);
     count_launch();
   }
   return cudaGetLastError();

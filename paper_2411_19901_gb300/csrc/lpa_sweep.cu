@@ -5,16 +5,16 @@
 
 namespace lpa {
 
-cudaError_t launch_sweep_warp(int mode, int k, bool weighted, const SweepArgs& a,
-                              const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
-  if (mode == kBM) return launch_warp_variants<BMState>(weighted, a, p, s, s_hub);
+cudaError_t launch_sweep_warp(int mode, int k, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s, cudaStream_t s_hub) {
+  if (mode == kBM) return launch_warp_variants<BMState, true>(a, p, s, s_hub);
   switch (k) {
-    case 1: return launch_warp_variants<MGSketch<1>>(weighted, a, p, s, s_hub);
-    case 2: return launch_warp_variants<MGSketch<2>>(weighted, a, p, s, s_hub);
-    case 4: return launch_warp_variants<MGSketch<4>>(weighted, a, p, s, s_hub);
-    case 8: return launch_warp_variants<MGSketch<8>>(weighted, a, p, s, s_hub);
-    case 16: return launch_sweep_mg16(weighted, a, p, s, s_hub);
-    case 32: return launch_sweep_mg32(weighted, a, p, s, s_hub);
+    case 1: return launch_warp_variants<MGSketch<1>>(a, p, s, s_hub);
+    case 2: return launch_warp_variants<MGSketch<2>>(a, p, s, s_hub);
+    case 4: return launch_warp_variants<MGSketch<4>>(a, p, s, s_hub);
+    case 8: return launch_warp_variants<MGSketch<8>, true>(a, p, s, s_hub);
+    case 16: return launch_sweep_mg16(a, p, s, s_hub);
+    case 32: return launch_sweep_mg32(a, p, s, s_hub);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -50,8 +50,9 @@ __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, 
 // Hub sweep: CTA c sweeps hub c, one leaf per thread, leaves merged by shuffles within
 // warps and through shared memory across warps.  Launched per hub class with CTAs of
 // max(32, L) threads, so every warp of a CTA holds leaves.
-template <class S, bool WT, bool RESCAN = false>
+template <class S, int WF, bool RESCAN = false>
 __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPlan p) {
+  constexpr bool WT = WF != kUnitW;
   if (a.done != nullptr && *a.done) return;
   __shared__ int sk[(kThreads / 32) * 32];
   __shared__ float sv[(kThreads / 32) * 32];
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
     const int64_t G = hub_leaf_groups(d, L);
     HubSliceAddr ad{p.hub_base[blockIdx.x] + (int64_t)(tid >> 5) * W * G + (tid & 31), W};
     const int ng = (int)((len + 3) >> 2);
-    fold_groups<S, WT, true>(st, p.sl_idx, p.sl_w, a.c_prev, v, (int)len, ng, ng, ad);
+    fold_groups<S, WF, false>(st, p, a.c_prev, -1, ng, ng, ad);
   }
   const int Lw = L < 32 ? L : 32;
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, tid < L && (lane & (2 * s - 1)) == 0);
@@ -142,10 +143,11 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
 // mid vertex whose L lanes are aligned inside the warp).  Lanes of one warp may belong to
 // vertices of different L: every lane runs the warp's largest L, merging only below its
 // own.  Warps are independent, so a CTA of kLaneThreads holds as few of them as possible.
-template <class S, bool WT, bool RESCAN = false>
-__global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
+template <class S, int WF, bool RESCAN = false, int TPB = kLaneThreads>
+__global__ void __launch_bounds__(TPB, 896 / TPB) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
+  constexpr bool WT = WF != kUnitW;
   if (a.done != nullptr && *a.done) return;
-  const int64_t q = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x;
+  const int64_t q = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int v = -1, leaf = 0, L = 1;
   int64_t lo = 0, len = 0;
@@ -172,8 +174,8 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
   // steps (the slice places are decided by warp votes)
   const int ngl = (int)((len + 3) >> 2);
   LaneSliceAddr ad{q < p.nlanes ? p.lane_base[q >> 5] : 0, ngl, (1u << lane) - 1u};
-  fold_groups<S, WT, true>(st, p.sl_idx, p.sl_w, a.c_prev, v, (int)len, act ? ngl : 0,
-                           __reduce_max_sync(kFullMask, ngl), ad);
+  fold_groups<S, WF, false>(st, p, a.c_prev, -1, act ? ngl : 0,
+                            __reduce_max_sync(kFullMask, ngl), ad);
   const int Lw = __reduce_max_sync(kFullMask, L);
   for (int s = 1; s < Lw; s <<= 1) st.shfl_merge(s, v >= 0 && s < L && (leaf & (2 * s - 1)) == 0);
   int choice = -1;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kLaneThreads, 7) sweep_lane_kernel(SweepArgs a
 // One sweep: the hub kernel on s_hub and the lane kernel on s (the caller orders the two
 // streams; they may be the same stream).  Both write disjoint entries of c_next and add to
 // the same dN counters.
-template <class S, bool WT, bool RESCAN = false>
+template <class S, int WF, bool RESCAN = false, bool SIZES = false>
 cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
                                cudaStream_t s_hub) {
   for (int c = 0; c < kHubClasses; ++c) {  // one launch per hub class, CTAs of 256 >> c
@@ -234,38 +236,51 @@ cudaError_t launch_warp_kernel(const SweepArgs& a, const WarpPlan& p, cudaStream
     WarpPlan q = p;
     q.hub_desc = p.hub_desc + p.hub_start[c];
     q.hub_base = p.hub_base + p.hub_start[c];
-    sweep_hub_kernel<S, WT, RESCAN><<<(unsigned)cnt, kThreads >> c, 0, s_hub>>>(a, q);
+    sweep_hub_kernel<S, WF, RESCAN><<<(unsigned)cnt, kThreads >> c, 0, s_hub>>>(a, q);
     count_launch();
   }
-  const int64_t lane_ctas = (p.nlanes + kLaneThreads - 1) / kLaneThreads;
+  // lane CTAs of the tuned size (built for the sketches that take every tuning)
+  const int tpb = SIZES ? p.lane_threads : kLaneThreads;
+  const int64_t lane_ctas = (p.nlanes + tpb - 1) / tpb;
   if (lane_ctas > 0) {
-    sweep_lane_kernel<S, WT, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    if constexpr (SIZES) {
+      if (tpb == 64)
+        sweep_lane_kernel<S, WF, RESCAN, 64><<<(unsigned)lane_ctas, 64, 0, s>>>(a, p);
+      else if (tpb == 256)
+        sweep_lane_kernel<S, WF, RESCAN, 256><<<(unsigned)lane_ctas, 256, 0, s>>>(a, p);
+      else
+        sweep_lane_kernel<S, WF, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    } else {
+      sweep_lane_kernel<S, WF, RESCAN><<<(unsigned)lane_ctas, kLaneThreads, 0, s>>>(a, p);
+    }
     count_launch();
   }
   return cudaGetLastError();
 }
 
-// The two instantiations of one sketch type: weighted or not.
-template <class S>
-cudaError_t launch_warp_variants(bool weighted, const SweepArgs& a, const WarpPlan& p,
-                                 cudaStream_t s, cudaStream_t s_hub) {
-  return weighted ? launch_warp_kernel<S, true>(a, p, s, s_hub)
-                  : launch_warp_kernel<S, false>(a, p, s, s_hub);
+// The instantiations of one sketch type: unit or fp32 weights; for the sketches that
+// full_tuning_sketch names (FULL) every lane CTA size.
+template <class S, bool FULL = false>
+cudaError_t launch_warp_variants(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                                 cudaStream_t s_hub) {
+  return p.wfmt == kSplitW ? launch_warp_kernel<S, kSplitW, false, FULL>(a, p, s, s_hub)
+                           : launch_warp_kernel<S, kUnitW, false, FULL>(a, p, s, s_hub);
 }
 
 // The MG ablation variants of one k: paper-literal accumulate and / or double scan.
 template <int K>
-cudaError_t launch_mg_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
-                              const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
+cudaError_t launch_mg_variant(bool literal, bool rescan, const SweepArgs& a, const WarpPlan& p,
+                              cudaStream_t s, cudaStream_t s_hub) {
+  const bool weighted = p.wfmt == kSplitW;
   if (literal) {
     if (rescan)
-      return weighted ? launch_warp_kernel<MGLiteral<K>, true, true>(a, p, s, s_hub)
-                      : launch_warp_kernel<MGLiteral<K>, false, true>(a, p, s, s_hub);
-    return weighted ? launch_warp_kernel<MGLiteral<K>, true, false>(a, p, s, s_hub)
-                    : launch_warp_kernel<MGLiteral<K>, false, false>(a, p, s, s_hub);
+      return weighted ? launch_warp_kernel<MGLiteral<K>, kSplitW, true>(a, p, s, s_hub)
+                      : launch_warp_kernel<MGLiteral<K>, kUnitW, true>(a, p, s, s_hub);
+    return weighted ? launch_warp_kernel<MGLiteral<K>, kSplitW, false>(a, p, s, s_hub)
+                    : launch_warp_kernel<MGLiteral<K>, kUnitW, false>(a, p, s, s_hub);
   }
-  return weighted ? launch_warp_kernel<MGSketch<K>, true, true>(a, p, s, s_hub)
-                  : launch_warp_kernel<MGSketch<K>, false, true>(a, p, s, s_hub);
+  return weighted ? launch_warp_kernel<MGSketch<K>, kSplitW, true>(a, p, s, s_hub)
+                  : launch_warp_kernel<MGSketch<K>, kUnitW, true>(a, p, s, s_hub);
 }
 
 }  // namespace lpa

@@ -3,9 +3,9 @@
 
 namespace lpa {
 
-cudaError_t launch_sweep_mg32(bool weighted, const SweepArgs& a, const WarpPlan& p,
-                              cudaStream_t s, cudaStream_t s_hub) {
-  return launch_warp_variants<MGSketch<32>>(weighted, a, p, s, s_hub);
+cudaError_t launch_sweep_mg32(const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
+                              cudaStream_t s_hub) {
+  return launch_warp_variants<MGSketch<32>>(a, p, s, s_hub);
 }
 
 }  // namespace lpa

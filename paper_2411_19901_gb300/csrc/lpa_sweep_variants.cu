@@ -6,16 +6,15 @@
 
 namespace lpa {
 
-cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, bool weighted,
-                                    const SweepArgs& a, const WarpPlan& p, cudaStream_t s,
-                                    cudaStream_t s_hub) {
+cudaError_t launch_sweep_mg_variant(int k, bool literal, bool rescan, const SweepArgs& a,
+                                    const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
   switch (k) {
-    case 1: return launch_mg_variant<1>(literal, rescan, weighted, a, p, s, s_hub);
-    case 2: return launch_mg_variant<2>(literal, rescan, weighted, a, p, s, s_hub);
-    case 4: return launch_mg_variant<4>(literal, rescan, weighted, a, p, s, s_hub);
-    case 8: return launch_mg_variant<8>(literal, rescan, weighted, a, p, s, s_hub);
-    case 16: return launch_sweep_mg16_variant(literal, rescan, weighted, a, p, s, s_hub);
-    case 32: return launch_sweep_mg32_variant(literal, rescan, weighted, a, p, s, s_hub);
+    case 1: return launch_mg_variant<1>(literal, rescan, a, p, s, s_hub);
+    case 2: return launch_mg_variant<2>(literal, rescan, a, p, s, s_hub);
+    case 4: return launch_mg_variant<4>(literal, rescan, a, p, s, s_hub);
+    case 8: return launch_mg_variant<8>(literal, rescan, a, p, s, s_hub);
+    case 16: return launch_sweep_mg16_variant(literal, rescan, a, p, s, s_hub);
+    case 32: return launch_sweep_mg32_variant(literal, rescan, a, p, s, s_hub);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -4,9 +4,9 @@
 
 namespace lpa {
 
-cudaError_t launch_sweep_mg32_variant(bool literal, bool rescan, bool weighted, const SweepArgs& a,
+cudaError_t launch_sweep_mg32_variant(bool literal, bool rescan, const SweepArgs& a,
                                      const WarpPlan& p, cudaStream_t s, cudaStream_t s_hub) {
-  return launch_mg_variant<32>(literal, rescan, weighted, a, p, s, s_hub);
+  return launch_mg_variant<32>(literal, rescan, a, p, s, s_hub);
 }
 
 }  // namespace lpa

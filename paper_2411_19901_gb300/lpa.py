@@ -94,6 +94,22 @@ class lpa_graph_stats(ctypes.Structure):
     ]
 
 
+class lpa_tuning(ctypes.Structure):
+    """Launch choices that never change a result (zero = default); see include/lpa.h."""
+    _fields_ = [
+        ("window", ctypes.c_int32),
+        ("lane_threads", ctypes.c_int32),
+        ("serial_hubs", ctypes.c_int32),
+    ]
+
+    def to_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "lpa_tuning":
+        return cls(**{f: int(d.get(f, 0)) for f, _ in cls._fields_})
+
+
 class lpa_options(ctypes.Structure):
     _fields_ = [
         ("pl_period", ctypes.c_int32),
@@ -104,6 +120,7 @@ class lpa_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("tuning", ctypes.POINTER(lpa_tuning)),
     ]
 
 
@@ -217,8 +234,15 @@ def lpa_options_init() -> lpa_options:
 
 def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=False,
                  modularity=False, labels_in=None, stream=None, workspace=None,
-                 workspace_bytes=0, prune=False, unclamped=False, rescan=False) -> lpa_options:
+                 workspace_bytes=0, prune=False, unclamped=False, rescan=False,
+                 tuning=None) -> lpa_options:
+    """Options for the calls below.  ``tuning``: an lpa_tuning or a dict of its fields (the
+    struct is kept alive by the returned options)."""
     o = lpa_options_init()
+    if tuning is not None:
+        t = tuning if isinstance(tuning, lpa_tuning) else lpa_tuning.from_dict(tuning)
+        o._tuning_ref = t
+        o.tuning = ctypes.pointer(t)
     o.pl_period = pl_period
     o.leaf_e0 = leaf_e0
     o.leaf_max = leaf_max

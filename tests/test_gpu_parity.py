@@ -304,3 +304,37 @@ def test_convergence_test_is_strict_on_the_device(lpa):
         ref = oracle.lpa(g.offsets, g.indices, None, mode=oracle.MG, rho=0, tol=tol, labels_in=lab)
         assert st["changed"] == ref["changed"].tolist() and st["iterations"] == ref["iterations"]
         assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+# The plan packs integer weights into the index words of its sliced copy when they fit the
+# bits the indices leave free (n = 3000: 12 index bits, so weights below 2^20) and reads
+# fp32 weights otherwise; both must give the oracle's bits.  Weights stay symmetric: each
+# is an elementwise map of an integer weight in 1..8.
+@pytest.mark.parametrize("weights", ["packed_max", "just_over", "fractional"])
+@pytest.mark.parametrize("mode", ["mg", "bm"])
+def test_weight_formats_match_oracle(lpa, weights, mode):
+    g = synth.random_graph(3000, 18, seed=41, wmax=8, power=2.1, hubs=[(7, 2900), (11, 300)],
+                           self_loops=0.03, zero_weights=0.02)
+    scale = {"packed_max": lambda x: x * 131071.0,    # largest 1048568 < 2^20
+             "just_over": lambda x: x * 131072.0,     # 8 * 2^17 = 2^20 does not fit
+             "fractional": lambda x: x + 0.25 * (x > 0)}[weights]
+    g.weights = scale(g.weights.astype(np.float64)).astype(np.float32)
+    off, idx, w = to_dev(g)
+    rng = np.random.default_rng(3)
+    plan = lpa.Plan(off, idx, w, mode=mode, k=8)
+    try:
+        for c_prev in (np.arange(g.n, dtype=np.int32),
+                       rng.integers(0, 40, size=g.n).astype(np.int32)):
+            cn = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            dn = plan.sweep(torch.from_numpy(c_prev).cuda(), cn, False)
+            want, want_dn = oracle.move(g.offsets, g.indices, g.weights, c_prev,
+                                        mode=OMODE[mode], k=8, threads=4)
+            assert np.array_equal(cn.cpu().numpy(), want) and dn == want_dn
+    finally:
+        plan.close()
+    labels, st = lpa.detect(off, idx, w, mode=mode, k=8, modularity=True)
+    ref = oracle.lpa(g.offsets, g.indices, g.weights, mode=OMODE[mode], k=8)
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    assert st["changed"] == ref["changed"].tolist()
+    assert q_close(st["modularity"],
+                   oracle.modularity(g.offsets, g.indices, g.weights, ref["labels"]))
