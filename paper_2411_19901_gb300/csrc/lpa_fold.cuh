@@ -477,13 +477,13 @@ __device__ __forceinline__ void fold_groups(S& st, const WarpPlan& pl,
     }
   };
   auto gather = [&](int4& X, const float4& W) { X = gather_slice<SELF_LOOPS>(lab, X, W, own); };
-  auto fold = [&](int4 C, float4 W) {
-#pragma unroll 1
-    for (int u = 0; u < 4; ++u) {
-      if (C.x >= 0) st.add(C.x, W.x);
-      C = make_int4(C.y, C.z, C.w, -1);
-      W = make_float4(W.y, W.z, W.w, 0.f);
-    }
+  // the four pushes of a group inlined (no register moves between them: measured faster
+  // than one push site in a loop for the sliced layout)
+  auto fold = [&](const int4& C, const float4& W) {
+    if (C.x >= 0) st.add(C.x, W.x);
+    if (C.y >= 0) st.add(C.y, W.y);
+    if (C.z >= 0) st.add(C.z, W.z);
+    if (C.w >= 0) st.add(C.w, W.w);
   };
   int4 X0, X1 = make_int4(-1, -1, -1, -1), X2 = make_int4(-1, -1, -1, -1);
   float4 W0, W1 = make_float4(0.f, 0.f, 0.f, 0.f), W2 = make_float4(0.f, 0.f, 0.f, 0.f);
