@@ -593,7 +593,7 @@ def run_ours(args):
     if SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha() and SWEEP_TRAFFIC["workload"] == args.workload:
         traffic = SWEEP_TRAFFIC["bytes_per_launch"]
     cpu = None
-    if world == 1:
+    if world == 1 and not args.skip_cpu:
         times, threads = oracle_sweeps(g, args.mode, seconds=10.0, max_reps=3, k=args.k,
                                        unclamped=args.unclamped, rescan=args.rescan)
         cpu = {"value": len(times) * m / sum(times), "unit": UNIT, "cores": threads,
@@ -1016,6 +1016,9 @@ def main():
                     help="MG ablation: the accumulate exactly as printed (LPA_MG_UNCLAMPED)")
     ap.add_argument("--rescan", action="store_true",
                     help="MG ablation: the double scan of Sec. 4.4 (LPA_RESCAN)")
+    ap.add_argument("--skip-cpu", action="store_true",
+                    help="leave out the oracle's cpu_baseline (for ablation tables; the "
+                         "default run always reports it)")
     ap.add_argument("--tune", action="store_true",
                     help="time the autotuner's candidates first and run the timed steps with "
                          "its pick (the default launch choices are timed beside it)")

@@ -148,7 +148,7 @@ struct Layout {
   size_t act, scanned, scan_total;  // pruning: two flag arrays, per-iteration counters
   // sketch modes
   size_t desc, wtab, hcnt, lcnt, hub_prefix, lane_prefix, hub_desc, lane_desc, counts;
-  size_t sl_cnt, sl_base, sl_idx, sl_w;  // the sliced copy of the CSR and its bases
+  size_t sl_cnt, sl_base, sl_tiles, sl_idx, sl_w;  // the sliced copy of the CSR, its bases
   int64_t hub_cap, lane_cap, sl_cap;
   // exact mode
   size_t cv0, cv1, hubs, hub_tab, seg;
@@ -197,6 +197,7 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int win, bool weighted,
     const int64_t nbase = L.lane_cap / 32 + L.hub_cap + 1;
     L.sl_cnt = take(sizeof(int32_t) * (size_t)nbase);
     L.sl_base = take(sizeof(int64_t) * (size_t)nbase);
+    L.sl_tiles = take(sizeof(int64_t) * (size_t)scan_tile_slots(nbase));
     L.sl_idx = take(sizeof(int4) * (size_t)L.sl_cap);
     L.sl_w = weighted ? take(sizeof(float4) * (size_t)L.sl_cap) : 0;
     WarpPlan dummy{};
@@ -416,7 +417,8 @@ lpa_status bin_classes(lpa_plan_s* p) {
   int64_t* base = (int64_t*)(p->ws + ly.sl_base);
   wp.lane_base = base;
   wp.hub_base = base + nlanes / 32;
-  LPA_CUDA(launch_slice_count(wp, p->e0, p->lmax, (int32_t*)(p->ws + ly.sl_cnt), base, s));
+  LPA_CUDA(launch_slice_count(wp, p->e0, p->lmax, (int32_t*)(p->ws + ly.sl_cnt), base,
+                              (int64_t*)(p->ws + ly.sl_tiles), s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls + 16, base + nlanes / 32 + nhubs, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));

@@ -232,8 +232,11 @@ size_t exact_smem_bytes(bool weighted);
 cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int win,
                                int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt,
                                cudaStream_t s);
-// prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.
-cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s);
+// prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.  With
+// tiles (scan_tile_slots(len) int64 scratch) long arrays are scanned by many CTAs.
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s,
+                               int64_t* tiles = nullptr);
+inline int64_t scan_tile_slots(int64_t len) { return len / 8192 + 2; }
 // Hub and lane descriptors of every window at their prefix offsets (hub_prefix over the
 // class-major hub counts; capacities bound the writes).
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
@@ -246,7 +249,7 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
 // and scans; pass 2 (after the host has checked the total against the capacity) fills
 // sl_idx / sl_w (sl_w null for unit weights).
 cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
-                               cudaStream_t s);
+                               int64_t* tiles, cudaStream_t s);
 cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
                               int e0, int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s);
 // Whether the sweeps are built with every lane CTA size of lpa_tuning (MG with k = 8 and

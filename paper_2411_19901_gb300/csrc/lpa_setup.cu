@@ -307,6 +307,118 @@ __global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(const int32_t
   if (tid == kScanThreads - 1) prefix[len] = sv[tid];
 }
 
+// Multi-CTA exclusive scan for long count arrays: tiles of kScanTile counts; pass 1 sums
+// each tile, scan_counts_kernel scans the tile sums, pass 2 scans each tile through
+// shared memory (coalesced loads and stores) and adds its tile's base.
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t* warp_sums,
+                                                        int64_t* total) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int64_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sums[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  const int64_t before = (wid > 0 ? warp_sums[wid - 1] : 0) + incl - x;
+  if (total) *total = warp_sums[31];
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) tile_sum_kernel(const int32_t* cnt, int64_t len,
+                                                                int64_t* sums) {
+  __shared__ int64_t ws[32];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+  int64_t x = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    const int64_t i = t0 + q * kScanThreads + threadIdx.x;
+    if (i < len) x += cnt[i];
+  }
+  int64_t total = 0;
+  block_exclusive_scan(x, ws, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const int32_t* cnt, int64_t len,
+                                                                 const int64_t* tile_base,
+                                                                 int64_t* prefix) {
+  __shared__ int32_t sc[kScanTile];
+  __shared__ int64_t ws[32];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {  // coalesced load of the tile
+    const int64_t i = t0 + q * kScanThreads + threadIdx.x;
+    sc[q * kScanThreads + threadIdx.x] = i < len ? cnt[i] : 0;
+  }
+  __syncthreads();
+  int32_t v[kScanPer];
+  int64_t x = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = sc[threadIdx.x * kScanPer + q];
+    x += v[q];
+  }
+  int64_t r = tile_base[blockIdx.x] + block_exclusive_scan(x, ws, nullptr);
+  __syncthreads();
+  int64_t* out = reinterpret_cast<int64_t*>(sc);  // the tile's prefixes, half a tile at a time
+  for (int half = 0; half < 2; ++half) {
+    const int lo = half * (kScanThreads / 2);
+    if (threadIdx.x >= lo && threadIdx.x < lo + kScanThreads / 2) {
+      int64_t rr = r;
+#pragma unroll
+      for (int q = 0; q < kScanPer; ++q) {
+        out[(threadIdx.x - lo) * kScanPer + q] = rr;
+        rr += v[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kScanPer / 2; ++q) {  // coalesced store
+      const int e = q * kScanThreads + threadIdx.x;
+      const int64_t i = t0 + (int64_t)lo * kScanPer + e;
+      if (i < len) prefix[i] = out[e];
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) prefix[len] = tile_base[gridDim.x];
+}
+
+// In-place exclusive prefix of len int64 values (len <= kScanThreads * kScanPer * 64 in
+// practice: tile sums), a[len] = total.
+__global__ void __launch_bounds__(kScanThreads) scan_i64_kernel(int64_t* a, int64_t len) {
+  __shared__ int64_t ws[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < len; b0 += kScanThreads) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t x = i < len ? a[i] : 0;
+    int64_t total = 0;
+    const int64_t ex = block_exclusive_scan(x, ws, &total);
+    const int64_t c = carry;
+    if (i < len) a[i] = c + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a[len] = carry;
+}
+
 // One CTA per window: copy the window's hub descriptors to hub_desc[hub_prefix[w] + i]
 // and write one lane descriptor per packed lane to lane_desc[lane_prefix[w] + q]:
 // {v, leaf start lo, leaf start hi, leaf length | leaf << kLaneLeafShift | log2 L <<
@@ -716,7 +828,18 @@ cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s) {
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s,
+                               int64_t* tiles) {
+  if (tiles && len > kScanTile) {
+    const int64_t ntiles = (len + kScanTile - 1) / kScanTile;
+    tile_sum_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(cnt, len, tiles);
+    count_launch();
+    scan_i64_kernel<<<1, kScanThreads, 0, s>>>(tiles, ntiles);  // tiles[0, ntiles] in place
+    count_launch();
+    tile_scan_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(cnt, len, tiles, prefix);
+    count_launch();
+    return cudaGetLastError();
+  }
   scan_counts_kernel<<<1, kScanThreads, 0, s>>>(cnt, len, prefix);
   count_launch();
   return cudaGetLastError();
@@ -735,7 +858,7 @@ cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int
 }
 
 cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
-                               cudaStream_t s) {
+                               int64_t* tiles, cudaStream_t s) {
   const int64_t nw = p.nlanes >> 5;
   const int64_t threads = ((p.nlanes + 255) >> 8 << 8) + p.nhubs;
   if (threads > 0) {
@@ -745,7 +868,7 @@ cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_scan_counts(cnt, nw + p.nhubs, base, s);
+  return launch_scan_counts(cnt, nw + p.nhubs, base, s, tiles);
 }
 
 cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
