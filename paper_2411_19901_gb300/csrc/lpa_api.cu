@@ -148,8 +148,10 @@ struct Layout {
   size_t act, scanned, scan_total;  // pruning: two flag arrays, per-iteration counters
   // sketch modes
   size_t desc, wtab, hcnt, lcnt, hub_prefix, lane_prefix, hub_desc, lane_desc, counts;
-  size_t sl_cnt, sl_base, sl_tiles, sl_idx, sl_w;  // the sliced copy of the CSR, its bases
-  int64_t hub_cap, lane_cap, sl_cap;
+  // the sliced copy of the CSR: lane warp counts and bases, hub counts, prefix and bases,
+  // scan scratch, the copies of the indices and weights
+  size_t sl_cnt, sl_base, sl_hcnt, sl_hpre, sl_hbase, sl_tmp, sl_tiles, sl_idx, sl_w;
+  int64_t hub_cap, lane_cap, sl_cap, nwin_cap;
   // exact mode
   size_t cv0, cv1, hubs, hub_tab, seg;
   // modularity
@@ -182,6 +184,7 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int win, bool weighted,
     L.partials = take(sizeof(double) * 3 * (size_t)modularity_partials((int32_t)n));
   } else {
     const int64_t nwin = num_windows(n, win);
+    L.nwin_cap = nwin;
     L.hub_cap = hub_cap(n, m, e0);
     L.lane_cap = lane_cap(n, m, e0, win);
     L.desc = take(sizeof(int4) * (size_t)(nwin * win));
@@ -194,10 +197,14 @@ Layout layout(int64_t n, int64_t m, int mode, int e0, int win, bool weighted,
     L.lane_desc = take(sizeof(int4) * (size_t)std::max<int64_t>(L.lane_cap, 1));
     L.counts = take(sizeof(unsigned long long) * 8);
     L.sl_cap = slice_cap(n, m, e0, win);
-    const int64_t nbase = L.lane_cap / 32 + L.hub_cap + 1;
-    L.sl_cnt = take(sizeof(int32_t) * (size_t)nbase);
-    L.sl_base = take(sizeof(int64_t) * (size_t)nbase);
-    L.sl_tiles = take(sizeof(int64_t) * (size_t)scan_tile_slots(nbase));
+    const int64_t nlw = L.lane_cap / 32 + 1, nmax = std::max<int64_t>(nlw, L.hub_cap) + 2;
+    L.sl_cnt = take(sizeof(int32_t) * (size_t)nlw);
+    L.sl_base = take(sizeof(int64_t) * (size_t)(nlw + 1));
+    L.sl_hcnt = take(sizeof(int32_t) * (size_t)(L.hub_cap + 1));
+    L.sl_hpre = take(sizeof(int64_t) * (size_t)(L.hub_cap + 2));
+    L.sl_hbase = take(sizeof(int64_t) * (size_t)(L.hub_cap + 1));
+    L.sl_tmp = take(sizeof(int64_t) * (size_t)nmax);
+    L.sl_tiles = take(sizeof(int64_t) * (size_t)scan_tile_slots(nmax));
     L.sl_idx = take(sizeof(int4) * (size_t)L.sl_cap);
     L.sl_w = weighted ? take(sizeof(float4) * (size_t)L.sl_cap) : 0;
     WarpPlan dummy{};
@@ -247,6 +254,7 @@ struct lpa_plan_s {
   int mode = kMG, k = 8;
   int e0 = 64, lmax = 256, rho = 8;
   lpa_tuning tune{};  // launch choices (all fields resolved: no zeros)
+  int64_t cap_n = 0, cap_m = 0;  // largest graph the workspace layout holds
   uint32_t flags = 0;
   const int32_t* labels_in = nullptr;
   cudaStream_t stream = nullptr;
@@ -357,7 +365,7 @@ void destroy_plan(lpa_plan_s* p) {
 
 // Window binning of the sketch modes: sort each window's vertices into groups, lay out
 // the hub and lane descriptors, and read back the totals.
-lpa_status bin_classes(lpa_plan_s* p) {
+lpa_status bin_classes(lpa_plan_s* p, int32_t keep_n) {
   cudaStream_t s = p->stream;
   const int32_t n = p->n;
   const Layout& ly = p->lay;
@@ -368,6 +376,9 @@ lpa_status bin_classes(lpa_plan_s* p) {
   if (n == 0) return LPA_OK;
   const int win = p->tune.window;
   const int32_t nwin = (int32_t)num_windows(n, win);
+  const int64_t hstride = ly.nwin_cap;
+  // windows before w0 hold only vertices below keep_n, binned before and unchanged
+  const int32_t w0 = keep_n > 0 ? keep_n / win : 0;
   int4* desc = (int4*)(p->ws + ly.desc);
   int32_t* wtab = (int32_t*)(p->ws + ly.wtab);
   int32_t* hcnt = (int32_t*)(p->ws + ly.hcnt);
@@ -378,27 +389,32 @@ lpa_status bin_classes(lpa_plan_s* p) {
   // counts: [0, 3) weight profile
   LPA_CUDA(launch_fill_u64(counts, 0ull, 8, s));
   LPA_CUDA(launch_fill_u64(counts, 1ull, 1, s));  // profile: all integral until shown otherwise
-  LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, win, desc, wtab, hcnt, lcnt, s));
-  LPA_CUDA(launch_scan_counts(hcnt, (int64_t)kHubClasses * nwin, hub_prefix, s));
+  for (int c = 0; c < kHubClasses; ++c)  // hub counts of the windows sorted now, and past them
+    LPA_CUDA(launch_fill_i32(hcnt + c * hstride + w0, 0, hstride - w0, s));
+  LPA_CUDA(launch_window_sort(p->off, n, p->e0, p->lmax, win, w0, hstride, desc, wtab, hcnt,
+                              lcnt, s));
+  LPA_CUDA(launch_scan_counts(hcnt, (int64_t)kHubClasses * hstride, hub_prefix, s));
   LPA_CUDA(launch_scan_counts(lcnt, nwin, lane_prefix, s));
-  LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, win, (int4*)wp.hub_desc,
-                               ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
+  LPA_CUDA(launch_expand_lanes(desc, wtab, hub_prefix, lane_prefix, nwin, win, hstride, w0,
+                               (int4*)wp.hub_desc, ly.hub_cap, (int4*)wp.lane_desc, ly.lane_cap, s));
   // the longest row (the weights are not read: only row lengths matter here)
   LPA_CUDA(launch_weight_profile(p->off, nullptr, n, p->m, counts, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls, counts, sizeof(unsigned long long) * 3,
                            cudaMemcpyDeviceToHost, s));
   for (int c = 0; c <= kHubClasses; ++c)  // first hub of each class, then the total
-    LPA_CUDA(cudaMemcpyAsync(p->host_cls + 8 + c, hub_prefix + (int64_t)c * nwin,
+    LPA_CUDA(cudaMemcpyAsync(p->host_cls + 8 + c, hub_prefix + (int64_t)c * hstride,
                              sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 3, hub_prefix + (int64_t)kHubClasses * nwin,
-                           sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaMemcpyAsync(p->host_cls + 4, lane_prefix + nwin, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 5, lane_prefix + w0, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
   const double dmax = (double)p->host_cls[2];
   if (dmax > 2147483647.0) return fail(LPA_EUNSUPPORTED, "a row has more than 2^31 - 1 entries");
-  const int64_t nhubs = (int64_t)p->host_cls[3], nlanes = (int64_t)p->host_cls[4];
-  if (nhubs < 0 || nhubs > ly.hub_cap || nlanes < 0 || nlanes > ly.lane_cap)
+  const int64_t nhubs = (int64_t)p->host_cls[8 + kHubClasses], nlanes = (int64_t)p->host_cls[4];
+  const int64_t lane_from = (int64_t)p->host_cls[5];
+  if (nhubs < 0 || nhubs > ly.hub_cap || nlanes < 0 || nlanes > ly.lane_cap || lane_from < 0 ||
+      lane_from > nlanes || (lane_from & 31))
     return fail(LPA_EINTERNAL, "window binning counted %lld hubs and %lld lanes", (long long)nhubs,
                 (long long)nlanes);
   const int64_t nctas = nhubs + (nlanes + kThreads - 1) / kThreads;
@@ -412,23 +428,28 @@ lpa_status bin_classes(lpa_plan_s* p) {
   wp.lane_threads = p->tune.lane_threads;
   p->nhubs = nhubs;
   p->nchunks = nctas - nhubs;
-  // the sliced copy of the CSR that the sweeps read
+  // the sliced copy of the CSR that the sweeps read (lanes from lane_from on, every hub)
   wp.wfmt = p->w ? kSplitW : kUnitW;
-  int64_t* base = (int64_t*)(p->ws + ly.sl_base);
-  wp.lane_base = base;
-  wp.hub_base = base + nlanes / 32;
-  LPA_CUDA(launch_slice_count(wp, p->e0, p->lmax, (int32_t*)(p->ws + ly.sl_cnt), base,
-                              (int64_t*)(p->ws + ly.sl_tiles), s));
-  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 16, base + nlanes / 32 + nhubs, sizeof(int64_t),
+  int64_t* lane_base = (int64_t*)(p->ws + ly.sl_base);
+  int64_t* hub_pre = (int64_t*)(p->ws + ly.sl_hpre);
+  wp.lane_base = lane_base;
+  wp.hub_base = (int64_t*)(p->ws + ly.sl_hbase);
+  LPA_CUDA(launch_slice_count(wp, p->e0, p->lmax, lane_from, (int32_t*)(p->ws + ly.sl_cnt),
+                              (int32_t*)(p->ws + ly.sl_hcnt), (int64_t*)(p->ws + ly.sl_tmp),
+                              (int64_t*)(p->ws + ly.sl_tiles), lane_base, hub_pre,
+                              (int64_t*)wp.hub_base, ly.sl_cap, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 16, lane_base + nlanes / 32, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+  LPA_CUDA(cudaMemcpyAsync(p->host_cls + 17, hub_pre + nhubs, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   LPA_CUDA(cudaStreamSynchronize(s));
-  const int64_t groups = (int64_t)p->host_cls[16];
-  if (groups < 0 || groups > ly.sl_cap)
-    return fail(LPA_EINTERNAL, "sliced copy of %lld groups exceeds its bound %lld",
-                (long long)groups, (long long)ly.sl_cap);
+  const int64_t lane_groups = (int64_t)p->host_cls[16], hub_groups = (int64_t)p->host_cls[17];
+  if (lane_groups < 0 || hub_groups < 0 || lane_groups + hub_groups > ly.sl_cap)
+    return fail(LPA_EINTERNAL, "sliced copy of %lld + %lld groups exceeds its bound %lld",
+                (long long)lane_groups, (long long)hub_groups, (long long)ly.sl_cap);
   wp.sl_idx = (const int4*)(p->ws + ly.sl_idx);
   wp.sl_w = p->w ? (const float4*)(p->ws + ly.sl_w) : nullptr;
-  LPA_CUDA(launch_slice_fill(p->idx, p->w, p->m, wp, p->e0, p->lmax, (int4*)wp.sl_idx,
+  LPA_CUDA(launch_slice_fill(p->idx, p->w, p->m, wp, p->e0, p->lmax, lane_from, (int4*)wp.sl_idx,
                              (float4*)wp.sl_w, s));
   return LPA_OK;
 }
@@ -482,9 +503,12 @@ lpa_status bin_chunks(lpa_plan_s* p, const lpa_options& o) {
   return LPA_OK;
 }
 
+// A plan of the graph (offsets, indices, weights, n, m).  Its workspace is laid out for
+// graphs of up to cap_n vertices and cap_m entries (at least n, m), so that the served
+// form can re-bind it to its grown arena (plan_rebind) without allocating.
 lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const float* weights,
                        int32_t n, int64_t m, lpa_mode mode, int32_t k, const lpa_options* opt,
-                       lpa_plan_s** out) {
+                       lpa_plan_s** out, int64_t cap_n = -1, int64_t cap_m = -1) {
   *out = nullptr;
   lpa_status s = check_graph_args(offsets, indices, n, m);
   if (s != LPA_OK) return s;
@@ -539,7 +563,9 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   p->host_cls = (unsigned long long*)(p->host_q + 4);
 
   // workspace: fixed part now; exact-mode hub tables once binning knows their size
-  p->lay = layout(n, m, p->mode, p->e0, p->tune.window, weights != nullptr,
+  p->cap_n = std::max<int64_t>(cap_n, n);
+  p->cap_m = std::max<int64_t>(cap_m, m);
+  p->lay = layout(p->cap_n, p->cap_m, p->mode, p->e0, p->tune.window, weights != nullptr,
                   p->mode == kExact ? 2 * m : 0);
   if (o.workspace) {
     if (o.workspace_bytes < p->lay.total)
@@ -591,7 +617,7 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
                        (err & kErrLabels) ? " labels_in out of range" : ""));
     }
   }
-  s = p->mode == kExact ? bin_chunks(p, o) : bin_classes(p);
+  s = p->mode == kExact ? bin_chunks(p, o) : bin_classes(p, 0);
   if (s != LPA_OK) return bail(s);
   if (p->mode != kExact && p->wp.nhubs > 0 && p->wp.nlanes > 0 && !p->tune.serial_hubs) {
     ce = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
@@ -608,6 +634,30 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
     p->setup_ms = ms;
   }
   *out = p;
+  return LPA_OK;
+}
+
+// Re-bind a sketch-mode plan to a grown graph whose first keep_n vertices (and their rows)
+// are unchanged: only the binning windows from the one holding vertex keep_n on, their
+// lanes and their slices, and the hubs are redone (keep_n = 0: everything).  The graph
+// must fit the plan's capacity and weight format; no validation, no timing.
+lpa_status plan_rebind(lpa_plan_s* p, const int64_t* offsets, const int32_t* indices,
+                       const float* weights, int32_t n, int64_t m, int32_t keep_n) {
+  if (p->mode == kExact || n > p->cap_n || m > p->cap_m || (weights && !p->lay.sl_w))
+    return fail(LPA_EINTERNAL, "plan cannot take this graph");
+  p->off = offsets;
+  p->idx = indices;
+  p->w = weights;
+  p->n = n;
+  p->m = m;
+  lpa_status s = bin_classes(p, keep_n);
+  if (s != LPA_OK) return s;
+  if (!p->side && p->wp.nhubs > 0 && p->wp.nlanes > 0 && !p->tune.serial_hubs) {
+    cudaError_t ce = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return fail(LPA_ECUDA, "side stream: %s", cudaGetErrorString(ce));
+  }
   return LPA_OK;
 }
 
@@ -812,6 +862,8 @@ struct Packing {
   int32_t* lab[2] = {nullptr, nullptr};
   int cur = 0;
   lpa_plan_s* plan = nullptr;
+  bool plan_ok = false;   // the plan bins the used part as it is now
+  int64_t binned_n = 0;   // vertices the plan's binning covers
 };
 
 // HBM a resident graph takes: packed CSR (8 B offset + 4 B index (+ 4 B weight) per entry),
@@ -954,19 +1006,41 @@ lpa_status append_graphs(Packing& P, const std::vector<ServeReq*>& rs, const int
 }
 
 // The plan over the packing's used part (rebuilt after every change of it).
-lpa_status replan(lpa_server_s* S) {
+// The plan over the packing's used part.  After an append (keep) only the binning windows
+// from the first appended vertex on, their lanes and slices, and the hubs are redone; after
+// a compaction, everything.  A sketch-mode plan that can hold the arena is re-bound in
+// place (its workspace, pinned blocks and streams are reused); otherwise a plan is created
+// for the arena's capacity.
+lpa_status replan(lpa_server_s* S, bool keep) {
   Packing& P = S->pk;
+  if (P.N == 0) {
+    P.plan_ok = false;
+    P.binned_n = 0;
+    return LPA_OK;
+  }
+  if (P.plan && S->mode != kExact && P.N <= P.plan->cap_n && P.M <= P.plan->cap_m &&
+      (!P.w || P.plan->lay.sl_w)) {
+    const int32_t keep_n = keep && P.plan_ok ? (int32_t)P.binned_n : 0;
+    const lpa_status s = plan_rebind(P.plan, P.off, P.idx, P.w, (int32_t)P.N, P.M, keep_n);
+    P.plan_ok = s == LPA_OK;
+    P.binned_n = P.plan_ok ? P.N : 0;
+    return s;
+  }
   if (P.plan) {
     destroy_plan(P.plan);
     P.plan = nullptr;
   }
-  if (P.N == 0) return LPA_OK;
+  P.plan_ok = false;
   lpa_options po = S->opt;
   po.flags &= ~(LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY | LPA_PRUNE);
   po.workspace = nullptr;
   po.workspace_bytes = 0;
   po.labels_in = nullptr;
-  return plan_create(P.off, P.idx, P.w, (int32_t)P.N, P.M, (lpa_mode)S->mode, S->k, &po, &P.plan);
+  const lpa_status s = plan_create(P.off, P.idx, P.w, (int32_t)P.N, P.M, (lpa_mode)S->mode, S->k,
+                                   &po, &P.plan, P.ncap, P.mcap);
+  P.plan_ok = s == LPA_OK;
+  P.binned_n = P.plan_ok ? P.N : 0;
+  return s;
 }
 
 // Admit fresh requests: append them if they fit the arena, else (or when dead slots hold
@@ -987,6 +1061,7 @@ lpa_status serve_admit(lpa_server_s* S, std::vector<ServeReq*>& fresh, bool comp
     lpa_status rs = append_graphs(P, fresh, nullptr, S->opt.pl_period, s);
     if (rs != LPA_OK) return rs;
     for (ServeReq* r : fresh) S->slots.push_back(r);
+    return replan(S, true);
   } else {
     std::vector<ServeReq*> live;
     int64_t lv = 0, le = 0;
@@ -1017,12 +1092,14 @@ lpa_status serve_admit(lpa_server_s* S, std::vector<ServeReq*>& fresh, bool comp
       free_packing(Q, s);
       return rs;
     }
+    Q.plan = P.plan;  // the plan moves to the new arena (re-bound below)
+    P.plan = nullptr;
     free_packing(P, s);
     S->pk = Q;
     S->slots = live;
     for (ServeReq* r : fresh) S->slots.push_back(r);
   }
-  return replan(S);
+  return replan(S, false);
 }
 
 lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
@@ -1056,12 +1133,12 @@ lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
     }
     if (rs != LPA_OK) return rs;
   }
-  if (S->live > 0 && !S->pk.plan) {  // a previous re-plan failed: try again
-    lpa_status rs = replan(S);
+  if (S->live > 0 && !S->pk.plan_ok) {  // a previous re-plan failed: try again
+    lpa_status rs = replan(S, false);
     if (rs != LPA_OK) return rs;
   }
   Packing& P = S->pk;
-  if (S->live == 0 || !P.plan) {
+  if (S->live == 0 || !P.plan_ok) {
     if (pending_out) *pending_out = (int32_t)S->waiting.size();
     return LPA_OK;
   }
@@ -1105,9 +1182,9 @@ lpa_status serve_step(lpa_server_s* S, int32_t* pending_out) {
       S->finished.push_back(r->ticket);
     }
   }
-  if (S->live == 0) {  // everything stopped: the arena is empty again
-    if (P.plan) destroy_plan(P.plan);
-    P.plan = nullptr;
+  if (S->live == 0) {  // everything stopped: the arena is empty again (its plan is kept)
+    P.plan_ok = false;
+    P.binned_n = 0;
     P.count = 0;
     P.N = P.M = P.dead_n = 0;
     S->slots.clear();

@@ -63,13 +63,16 @@ struct MGSketch {
 #pragma unroll
         for (int s = 0; s < h; ++s) lo[s] = fminf(lo[s], lo[s + h]);
       const float delta = fminf(w, lo[0]);
+      // slots that drop to zero become empty; the mask is built with predicated adds,
+      // which the compiler can put on the FMA pipe instead of the integer ALU pipe
       unsigned z = 0;
 #pragma unroll
       for (int s = 0; s < K; ++s) {
         val[s] = val[s] - delta;
-        const bool zero = (val[s] == 0.f);
-        if (zero) key[s] = -1;
-        z |= (zero ? 1u : 0u) << s;
+        if (val[s] == 0.f) {
+          key[s] = -1;
+          z = z + (1u << s);
+        }
       }
       em = z;
       w = w - delta;
@@ -466,11 +469,28 @@ __device__ __forceinline__ void fold_groups(S& st, const WarpPlan& pl,
   if (iters <= 0) return;
   const int4* __restrict__ si = pl.sl_idx;
   const float4* __restrict__ sw = pl.sl_w;
+  // the sliced copy is read once per sweep, a warp's loads covering whole lines: mark it
+  // first to leave L2 so that more of the gathered label array stays cached
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  auto stream = [&](const int4* q) {
+    int4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(q), "l"(pol));
+    return r;
+  };
   auto load = [&](int k, int4& X, float4& W) {
     const int64_t p = addr.at(k);
     if (k < ng) {
-      X = __ldg(si + p);
-      W = WF == kSplitW ? __ldg(sw + p) : make_float4(1.f, 1.f, 1.f, 1.f);
+      X = stream(si + p);
+      if (WF == kSplitW) {
+        const int4 t = stream(reinterpret_cast<const int4*>(sw + p));
+        W = make_float4(__int_as_float(t.x), __int_as_float(t.y), __int_as_float(t.z),
+                        __int_as_float(t.w));
+      } else {
+        W = make_float4(1.f, 1.f, 1.f, 1.f);
+      }
     } else {
       X = make_int4(-1, -1, -1, -1);
       W = make_float4(0.f, 0.f, 0.f, 0.f);

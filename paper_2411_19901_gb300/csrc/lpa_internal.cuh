@@ -229,9 +229,11 @@ size_t exact_smem_bytes(bool weighted);
 // Binning for the warp-per-row kernels.  Per window: sort the vertices into groups, write
 // their descriptors, the window table, the hub count of each class (class-major:
 // hcnt[c * nwin + window]) and the padded lane count.
+// Windows w_first .. ceil(n / win) - 1 only (the tables of earlier windows are kept);
+// hub counts are class-major with stride hstride (>= the number of windows).
 cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int win,
-                               int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt,
-                               cudaStream_t s);
+                               int32_t w_first, int64_t hstride, int4* desc, int32_t* wtab,
+                               int32_t* hcnt, int32_t* lcnt, cudaStream_t s);
 // prefix[0, len] = exclusive prefix sums of cnt[0, len), prefix[len] the total.  With
 // tiles (scan_tile_slots(len) int64 scratch) long arrays are scanned by many CTAs.
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix, cudaStream_t s,
@@ -239,19 +241,24 @@ cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix,
 inline int64_t scan_tile_slots(int64_t len) { return len / 8192 + 2; }
 // Hub and lane descriptors of every window at their prefix offsets (hub_prefix over the
 // class-major hub counts; capacities bound the writes).
+// Every window's hubs; lanes of windows w_lanes .. nwin - 1 only.
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
-                                const int64_t* lane_prefix, int32_t nwin, int win, int4* hub_desc,
-                                int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
-                                cudaStream_t s);
-// Sliced copy of the CSR for a binned plan (lpa_setup.cu).  cnt: nlanes / 32 + nhubs
-// int32 scratch; base: their exclusive prefix (nlanes / 32 + nhubs + 1 int64), so
-// base[nlanes / 32 + h] is hub h's first element and base[end] the total.  Pass 1 counts
-// and scans; pass 2 (after the host has checked the total against the capacity) fills
-// sl_idx / sl_w (sl_w null for unit weights).
-cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
-                               int64_t* tiles, cudaStream_t s);
+                                const int64_t* lane_prefix, int32_t nwin, int win, int64_t hstride,
+                                int32_t w_lanes, int4* hub_desc, int64_t hub_cap, int4* lane_desc,
+                                int64_t lane_cap, cudaStream_t s);
+// Sliced copy of the CSR for a binned plan (lpa_setup.cu), for the lanes from lane_from
+// on (a multiple of 32; the slices of the lanes before it are kept) and every hub.  Pass 1
+// counts each lane warp's groups into lane_cnt and each hub's into hub_cnt, continues
+// lane_base (lanes grow from element 0 up; lane_base[nlanes / 32] ends them) and fills
+// hub_base (hubs fill the top of `cap` elements downwards; hub_pre[nhubs] is their total).
+// Pass 2 (after the host has checked the totals against cap) copies the positions.
+cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int64_t lane_from,
+                               int32_t* lane_cnt, int32_t* hub_cnt, int64_t* scan_tmp,
+                               int64_t* tiles, int64_t* lane_base, int64_t* hub_pre,
+                               int64_t* hub_base, int64_t cap, cudaStream_t s);
 cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
-                              int e0, int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s);
+                              int e0, int lmax, int64_t lane_from, int4* sl_idx, float4* sl_w,
+                              cudaStream_t s);
 // Whether the sweeps are built with every lane CTA size of lpa_tuning (MG with k = 8 and
 // BM; the other sketches and the MG ablations use the default).
 inline bool full_tuning_sketch(int mode, int k) { return mode == kBM || (mode == kMG && k == 8); }

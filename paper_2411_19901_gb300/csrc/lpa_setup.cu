@@ -1,6 +1,8 @@
 // lpa_setup.cu -- everything around the sweep: CSR validation, degree binning into
 // chunks and hubs, label initialisation and the on-device convergence test (Alg. 1,
 // `lpa`).
+#include <algorithm>
+
 #include "lpa_internal.cuh"
 
 namespace lpa {
@@ -202,8 +204,8 @@ static_assert(kSortKeys <= kSortPad, "sort keys exceed the scan space");
 // table, the window's hub count and its lane count rounded up to whole warps.  Order
 // inside one key does not matter.
 __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
-    const int64_t* off, int32_t n, int e0, int lmax, int win, int4* desc, int32_t* wtab,
-    int32_t* hcnt, int32_t* lcnt) {
+    const int64_t* off, int32_t n, int e0, int lmax, int win, int32_t w_first, int64_t hstride,
+    int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt) {
   __shared__ int s_hist[kSortPad];
   __shared__ int s_wsum[kSortThreads / 32];
   __shared__ int s_grp[kHubClasses + kLaneGroups];  // hub classes, mid classes, low rows
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
   const int tid = threadIdx.x;
   for (int i = tid; i < kSortPad; i += kSortThreads) s_hist[i] = 0;
   __syncthreads();
-  const int64_t v0 = (int64_t)blockIdx.x * win;
+  const int64_t wi = (int64_t)w_first + blockIdx.x;  // the window this CTA sorts
+  const int64_t v0 = wi * win;
   int key[kPer];
   int64_t b[kPer];
   int d[kPer];
@@ -253,11 +256,11 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
   s_hist[2 * tid] = ex;
   s_hist[2 * tid + 1] = ex + x0;
   if (tid == 0) {
-    int32_t* t = wtab + (int64_t)blockIdx.x * kWinTab;
+    int32_t* t = wtab + wi * kWinTab;
     int nh = 0;
     for (int c = 0; c < kHubClasses; ++c) {
       t[kTabHub + c] = nh;
-      hcnt[(int64_t)c * gridDim.x + blockIdx.x] = s_grp[c];
+      hcnt[(int64_t)c * hstride + wi] = s_grp[c];
       nh += s_grp[c];
     }
     int lanes = 0, slot = nh;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kSortThreads) window_sort_kernel(
     }
     t[0] = nh;
     t[kTabLanes] = lanes;
-    lcnt[blockIdx.x] = (lanes + 31) & ~31;
+    lcnt[wi] = (lanes + 31) & ~31;
   }
   __syncthreads();
 #pragma unroll
@@ -426,7 +429,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_i64_kernel(int64_t* a, int6
 // (the host then refuses the plan).
 __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
     const int4* desc, const int32_t* wtab, const int64_t* hub_prefix, const int64_t* lane_prefix,
-    int win, int4* hub_desc, int64_t hub_cap, int4* lane_desc, int64_t lane_cap) {
+    int win, int64_t hstride, int32_t w_lanes, int4* hub_desc, int64_t hub_cap, int4* lane_desc,
+    int64_t lane_cap) {
   __shared__ int32_t t[kWinTab];
   const int tid = threadIdx.x;
   const int64_t wi = blockIdx.x;
@@ -437,9 +441,10 @@ __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
   for (int i = tid; i < nh; i += kSortThreads) {
     int c = kHubClasses - 1;  // the class whose slots hold i
     while (c > 0 && t[kTabHub + c] > i) --c;
-    const int64_t pos = hub_prefix[(int64_t)c * gridDim.x + wi] + (i - t[kTabHub + c]);
+    const int64_t pos = hub_prefix[(int64_t)c * hstride + wi] + (i - t[kTabHub + c]);
     if (pos < hub_cap) hub_desc[pos] = wd[i];
   }
+  if (wi < w_lanes) return;  // lanes of this window are kept from an earlier binning
   const int lanes = t[kTabLanes];
   const int64_t l0 = lane_prefix[wi];
   const int padded = (int)(lane_prefix[wi + 1] - l0);
@@ -567,27 +572,47 @@ __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long value,
 
 // ------------------------------------------------- sliced copy of the CSR
 
-// Pass 1: the groups of each lane warp's slice (the sum of its lanes' ceil(len / 4)) and
-// of each hub's slice (L leaves x the groups of its longest leaf).
+// Pass 1: the groups of each lane warp's slice (the sum of its lanes' ceil(len / 4)), for
+// lane warps w_from .. nlanes / 32 - 1, and of each hub's slice (L leaves x the groups of
+// its longest leaf).
 __global__ void __launch_bounds__(256) slice_count_kernel(const int4* __restrict__ lane_desc,
-                                                         int64_t nlanes,
+                                                         int64_t lane_from, int64_t nlanes,
                                                          const int4* __restrict__ hub_desc,
                                                          int32_t nhubs, int e0, int lmax,
-                                                         int32_t* cnt) {
+                                                         int32_t* lane_cnt, int32_t* hub_cnt) {
+  const int64_t span = ((nlanes - lane_from + 255) >> 8) << 8;  // lane threads, whole CTAs
   const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  const int64_t nw = nlanes >> 5;
-  if (t < nlanes) {  // whole warps: nlanes is a multiple of 32
-    const int4 l = __ldg(lane_desc + t);
+  const int64_t q = lane_from + t;
+  if (t < span && q < nlanes) {  // whole warps: lane_from and nlanes are multiples of 32
+    const int4 l = __ldg(lane_desc + q);
     const int g = l.x >= 0 ? ((l.w & ((1 << kLaneLeafShift) - 1)) + 3) >> 2 : 0;
     const int sum = __reduce_add_sync(0xffffffffu, g);
-    if ((threadIdx.x & 31) == 0) cnt[t >> 5] = sum;
+    if ((threadIdx.x & 31) == 0) lane_cnt[(q - lane_from) >> 5] = sum;
   }
-  const int64_t h = t - (((nlanes + 255) >> 8) << 8);  // hubs after the lane blocks
+  const int64_t h = t - span;  // hubs after the lane CTAs
   if (h >= 0 && h < nhubs) {
     const int64_t d = __ldg(hub_desc + h).w;
     const int L = leaf_count(d, e0, lmax);
-    cnt[nw + h] = (int32_t)(L * hub_leaf_groups(d, L));
+    hub_cnt[h] = (int32_t)(L * hub_leaf_groups(d, L));
   }
+}
+
+// base[w_from + i] = base[w_from] + scan[i] for i <= len (base[0] = 0 when w_from = 0):
+// the lane warps from w_from on continue after the kept ones.
+__global__ void lane_base_kernel(const int64_t* scan, int64_t len, int64_t w_from, int64_t* base) {
+  const int64_t start = w_from > 0 ? base[w_from] : 0;  // unchanged by this kernel
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= len; i += stride)
+    if (i > 0 || w_from == 0) base[w_from + i] = start + scan[i];
+}
+
+// Hub slices fill the top of the sliced copy downwards: hub h starts at
+// cap - total + pre[h], so lanes can grow from the bottom without moving them.
+__global__ void hub_base_kernel(const int64_t* pre, int32_t nhubs, int64_t cap, int64_t* hub_base) {
+  const int64_t total = pre[nhubs];
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nhubs;
+       h += (int64_t)gridDim.x * blockDim.x)
+    hub_base[h] = cap - total + pre[h];
 }
 
 // The aligned block of four CSR positions starting at a (a multiple of 4); positions at
@@ -633,10 +658,10 @@ __device__ __forceinline__ void store_group(const int (&j)[4], const int (&x)[4]
 template <int WF>
 __global__ void __launch_bounds__(256) slice_fill_lanes_kernel(
     const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t m,
-    const int4* __restrict__ lane_desc, int64_t nlanes, const int64_t* __restrict__ base,
-    int4* si, float4* sw) {
+    const int4* __restrict__ lane_desc, int64_t lane_from, int64_t nlanes,
+    const int64_t* __restrict__ base, int4* si, float4* sw) {
   constexpr bool WT = WF != kUnitW;
-  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t t = lane_from + (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (t >= nlanes) return;  // whole warps
   const int lane = threadIdx.x & 31;
   const int4 l = __ldg(lane_desc + t);
@@ -819,11 +844,12 @@ cudaError_t launch_weight_profile(const int64_t* off, const float* w, int32_t n,
 }
 
 cudaError_t launch_window_sort(const int64_t* off, int32_t n, int e0, int lmax, int win,
-                               int4* desc, int32_t* wtab, int32_t* hcnt, int32_t* lcnt,
-                               cudaStream_t s) {
-  const unsigned nwin = (unsigned)((n + (int64_t)win - 1) / win);
-  if (nwin == 0) return cudaSuccess;
-  window_sort_kernel<<<nwin, kSortThreads, 0, s>>>(off, n, e0, lmax, win, desc, wtab, hcnt, lcnt);
+                               int32_t w_first, int64_t hstride, int4* desc, int32_t* wtab,
+                               int32_t* hcnt, int32_t* lcnt, cudaStream_t s) {
+  const int64_t nwin = (n + (int64_t)win - 1) / win;
+  if (nwin <= w_first) return cudaSuccess;
+  window_sort_kernel<<<(unsigned)(nwin - w_first), kSortThreads, 0, s>>>(
+      off, n, e0, lmax, win, w_first, hstride, desc, wtab, hcnt, lcnt);
   count_launch();
   return cudaGetLastError();
 }
@@ -846,37 +872,54 @@ cudaError_t launch_scan_counts(const int32_t* cnt, int64_t len, int64_t* prefix,
 }
 
 cudaError_t launch_expand_lanes(const int4* desc, const int32_t* wtab, const int64_t* hub_prefix,
-                                const int64_t* lane_prefix, int32_t nwin, int win, int4* hub_desc,
-                                int64_t hub_cap, int4* lane_desc, int64_t lane_cap,
-                                cudaStream_t s) {
+                                const int64_t* lane_prefix, int32_t nwin, int win, int64_t hstride,
+                                int32_t w_lanes, int4* hub_desc, int64_t hub_cap, int4* lane_desc,
+                                int64_t lane_cap, cudaStream_t s) {
   if (nwin == 0) return cudaSuccess;
-  expand_lanes_kernel<<<(unsigned)nwin, kSortThreads, 0, s>>>(desc, wtab, hub_prefix, lane_prefix,
-                                                              win, hub_desc, hub_cap, lane_desc,
-                                                              lane_cap);
+  expand_lanes_kernel<<<(unsigned)nwin, kSortThreads, 0, s>>>(
+      desc, wtab, hub_prefix, lane_prefix, win, hstride, w_lanes, hub_desc, hub_cap, lane_desc,
+      lane_cap);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int32_t* cnt, int64_t* base,
-                               int64_t* tiles, cudaStream_t s) {
-  const int64_t nw = p.nlanes >> 5;
-  const int64_t threads = ((p.nlanes + 255) >> 8 << 8) + p.nhubs;
+cudaError_t launch_slice_count(const WarpPlan& p, int e0, int lmax, int64_t lane_from,
+                               int32_t* lane_cnt, int32_t* hub_cnt, int64_t* scan_tmp,
+                               int64_t* tiles, int64_t* lane_base, int64_t* hub_pre,
+                               int64_t* hub_base, int64_t cap, cudaStream_t s) {
+  const int64_t span = ((p.nlanes - lane_from + 255) >> 8) << 8;
+  const int64_t threads = span + p.nhubs;
   if (threads > 0) {
     slice_count_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        p.lane_desc, p.nlanes, p.hub_desc, p.nhubs, e0, lmax, cnt);
+        p.lane_desc, lane_from, p.nlanes, p.hub_desc, p.nhubs, e0, lmax, lane_cnt, hub_cnt);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_scan_counts(cnt, nw + p.nhubs, base, s, tiles);
+  const int64_t nw = (p.nlanes - lane_from) / 32, w_from = lane_from / 32;
+  cudaError_t e = launch_scan_counts(lane_cnt, nw, scan_tmp, s, tiles);
+  if (e != cudaSuccess) return e;
+  lane_base_kernel<<<(unsigned)std::min<int64_t>((nw + 256) / 256, 4096), 256, 0, s>>>(
+      scan_tmp, nw, w_from, lane_base);
+  count_launch();
+  e = launch_scan_counts(hub_cnt, p.nhubs, hub_pre, s, tiles);
+  if (e != cudaSuccess) return e;
+  if (p.nhubs > 0) {
+    hub_base_kernel<<<(unsigned)std::min<int64_t>((p.nhubs + 255) / 256, 4096), 256, 0, s>>>(
+        hub_pre, p.nhubs, cap, hub_base);
+    count_launch();
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_slice_fill(const int32_t* idx, const float* w, int64_t m, const WarpPlan& p,
-                              int e0, int lmax, int4* sl_idx, float4* sl_w, cudaStream_t s) {
-  if (p.nlanes > 0) {
-    const unsigned grid = (unsigned)((p.nlanes + 255) / 256);
+                              int e0, int lmax, int64_t lane_from, int4* sl_idx, float4* sl_w,
+                              cudaStream_t s) {
+  if (p.nlanes > lane_from) {
+    const unsigned grid = (unsigned)((p.nlanes - lane_from + 255) / 256);
     auto kern = p.wfmt == kSplitW ? slice_fill_lanes_kernel<kSplitW> : slice_fill_lanes_kernel<kUnitW>;
-    kern<<<grid, 256, 0, s>>>(idx, w, m, p.lane_desc, p.nlanes, p.lane_base, sl_idx, sl_w);
+    kern<<<grid, 256, 0, s>>>(idx, w, m, p.lane_desc, lane_from, p.nlanes, p.lane_base, sl_idx,
+                              sl_w);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

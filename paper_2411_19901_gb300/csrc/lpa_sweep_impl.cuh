@@ -143,8 +143,17 @@ __global__ void __launch_bounds__(kThreads) sweep_hub_kernel(SweepArgs a, WarpPl
 // mid vertex whose L lanes are aligned inside the warp).  Lanes of one warp may belong to
 // vertices of different L: every lane runs the warp's largest L, merging only below its
 // own.  Warps are independent, so a CTA of kLaneThreads holds as few of them as possible.
+// CTAs of 128 lane threads an SM should hold for sketch S: 7 (72 registers a thread) fits
+// the sketches up to k = 8; the 16- and 32-slot sketches need more registers than that
+// (they would spill), so fewer CTAs.
+template <class S>
+constexpr int lane_min_blocks() {
+  return S::kSlots >= 32 ? 3 : (S::kSlots >= 16 ? 5 : 7);
+}
+
 template <class S, int WF, bool RESCAN = false, int TPB = kLaneThreads>
-__global__ void __launch_bounds__(TPB, 896 / TPB) sweep_lane_kernel(SweepArgs a, WarpPlan p) {
+__global__ void __launch_bounds__(TPB, lane_min_blocks<S>() * 128 / TPB)
+    sweep_lane_kernel(SweepArgs a, WarpPlan p) {
   constexpr bool WT = WF != kUnitW;
   if (a.done != nullptr && *a.done) return;
   const int64_t q = (int64_t)blockIdx.x * TPB + threadIdx.x;

@@ -114,13 +114,17 @@ def test_server_edge_cases(lpa):
         lpa.Server(mode="mg", prune=True)
 
 
-def test_arena_appends_compacts_and_drains(lpa):
+@pytest.mark.parametrize("window", [0, 2048])
+def test_arena_appends_compacts_and_drains(lpa, window):
     """Thirty requests over thirty steps: the arena appends, leaves dead slots, compacts;
-    drain lists exactly the finished tickets and every result matches the oracle."""
+    drain lists exactly the finished tickets and every result matches the oracle.  With
+    2048-vertex binning windows most appends keep the windows before the new graph (only
+    the rest is re-binned), so the kept and the redone parts must fit together."""
     gs = [synth.sbm_member(g, seed=4, nmin=100, nmax=2500) for g in range(30)]
+    gs[7] = synth.random_graph(3000, 10, seed=5, wmax=6, power=2.2, hubs=[(3, 4500), (9, 700)])
     refs = [oracle.lpa(g.offsets, g.indices, g.weights, mode=oracle.MG, threads=4) for g in gs]
     outs = {}
-    with lpa.Server(mode="mg") as srv:
+    with lpa.Server(mode="mg", tuning={"window": window}) as srv:
         inflight = {}
         for step in range(400):
             if step < 30:
