@@ -52,18 +52,20 @@ def metric_name(args) -> str:
         name = {"bm": "BM", "exact": "exact"}[args.mode]
     return f"{name}-LPA edges/sec/iteration"
 
-# DRAM traffic of one sweep (its hub and lane kernels together) measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the workload named below, and the
-# hash of the sweep kernel source it was taken with.  If the source changes, traffic is
-# reported as null until a new capture is taken.
-SWEEP_TRAFFIC = {"src_sha256": "c5549dde830ca87d7bd454ca4252934ca9e06b29a4417297fc850c5bbeff8d4d", "workload": "lfr26",
-                 "bytes_per_launch": 37525691989}
+# DRAM traffic of one MG k = 8 sweep (its hub and lane kernels together) measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, each kernel launched alone with cold
+# caches) on the workload named below, and the hash of the sweep kernel source it was
+# taken with.  If the source changes, traffic is reported as null until a new capture.
+SWEEP_TRAFFIC = {"src_sha256": "e936b074759fb3a6fcb1ceef6f3959ce2f529c3efdd94ad68251e13e8ff43202", "workload": "lfr26",
+                 "bytes_per_launch": 31384872960}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
              "[4, 65536], community sizes power law 1.5 on [20, 1e6], mu=0.2, integer "
              "weights 1..8, community-contiguous ids, seed 0",
     "lfr22": "LFR-style heavy-tailed planted partition as lfr26 but n=2^22 (profiling size)",
+    "lfr26s": "LFR-style as lfr26 but degrees power law 2.1 on [2, 32] (mean about 5): a "
+              "profiling size whose label array (256 MB) still exceeds L2",
     "rmat22": "R-MAT scale 22, edge factor 16, (a,b,c)=(0.57,0.19,0.19), symmetrised, "
               "duplicates merged with summed weights, seed 0",
     "pp1000": "planted partition, 1000 vertices in 10 communities, p_in=0.1, p_out=0.005, "
@@ -86,6 +88,9 @@ SERVE_METRIC = "MG8-LPA served p99 latency"
 def make_graph(name: str, threads: int | None = None) -> synth.Graph:
     if name == "lfr26":
         return synth.lfr(n=2**26, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
+                         cmax=10**6, mu=0.2, wmax=8, seed=0, threads=threads)
+    if name == "lfr26s":
+        return synth.lfr(n=2**26, gamma_d=2.1, dmin=2, dmax=32, gamma_c=1.5, cmin=20,
                          cmax=10**6, mu=0.2, wmax=8, seed=0, threads=threads)
     if name == "lfr22":
         return synth.lfr(n=2**22, gamma_d=2.1, dmin=4, dmax=65536, gamma_c=1.5, cmin=20,
@@ -204,7 +209,7 @@ def physical_gpu_index(local_rank: int) -> int:
 
 
 # Approximate host bytes of each workload's CSR (offsets, indices, weights).
-GRAPH_BYTES = {"lfr26": 13 << 30, "rmat22": 2 << 30}
+GRAPH_BYTES = {"lfr26": 13 << 30, "lfr26s": 6 << 30, "rmat22": 2 << 30}
 
 
 def _bcast_from_rank0(obj):
@@ -279,6 +284,21 @@ def sweep_bytes(n: int, m: int, weighted: bool) -> int:
     neighbour label (12 B, 8 B with unit weights); per vertex its offset, old label, new
     label and its place in the degree order (8 + 4 + 4 + 4 = 20 B)."""
     return (12 if weighted else 8) * m + 20 * n
+
+
+def sweep_kernel_label(args, weighted: bool) -> str:
+    """The kernels one timed sweep launches, for the roofline line."""
+    wf = "weighted" if weighted else "unit weights"
+    if args.mode == "exact":
+        return f"one sweep: sweep_exact_kernel (per-vertex hashtable, {wf})"
+    if args.mode == "bm":
+        sk = "BMState"
+    else:
+        sk = f"MGLiteral<{args.k}>" if args.unclamped else f"MGSketch<{args.k}>"
+        if args.rescan:
+            sk += ", rescan"
+    return (f"one sweep: sweep_hub_kernel and sweep_lane_kernel <{sk}, {wf}> "
+            "(concurrent, fork/join)")
 
 
 def oracle_sweeps(g: synth.Graph, mode: str, seconds: float, max_reps: int, k: int = 8,
@@ -590,7 +610,9 @@ def run_ours(args):
     alg_bytes = sweep_bytes(n, m, weighted) + (sweep_bytes(0, m, weighted) if args.rescan else 0)
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     traffic = None
-    if SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha() and SWEEP_TRAFFIC["workload"] == args.workload:
+    default_sketch = args.mode == "mg" and args.k == 8 and not (args.unclamped or args.rescan)
+    if (default_sketch and SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha()
+            and SWEEP_TRAFFIC["workload"] == args.workload):
         traffic = SWEEP_TRAFFIC["bytes_per_launch"]
     cpu = None
     if world == 1 and not args.skip_cpu:
@@ -610,8 +632,7 @@ def run_ours(args):
         "config": config_of(args, g),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "one sweep: sweep_hub_kernel and sweep_lane_kernel "
-                               "<MGSketch<8>, weighted> (concurrent, fork/join)",
+                     "kernel": sweep_kernel_label(args, weighted),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs",
                      # the second fraction: measured DRAM bytes of one sweep over its time
@@ -770,7 +791,7 @@ def run_batch(args):
     if rank != 0:
         return
     iters = [s["iterations"] for s in stats]
-    useful = sum(it * (8 * g.m + 16 * g.n) for it, g in zip(iters, gs))
+    useful = sum(it * sweep_bytes(g.n, g.m, g.weights is not None) for it, g in zip(iters, gs))
     cpu = None
     if world == 1:
         rate, done, dt, threads = oracle_batch_rate(gs, args.mode, 10.0)
@@ -793,7 +814,7 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": useful / (step_ms * 1e-3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": useful / (step_ms * 1e-3) / 1e9 / peak,
                      "traffic": None, "kernel": "whole batched step (useful sweep bytes: "
-                     "sum over graphs of its iterations x (8 m + 16 n))",
+                     "sum over graphs of its iterations x (8 or 12) m + 20 n)",
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_graphs_all / (e2e_ms * 1e-3), "unit": "graphs/s",

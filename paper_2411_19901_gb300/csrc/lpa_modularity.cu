@@ -234,17 +234,34 @@ __global__ void __launch_bounds__(256) modularity_total_kernel(const double* a_p
 // ------------------------------------------------------- standalone pass (no binning)
 //
 // A warp takes a tile of 32 consecutive vertices.  A row of at most kModShortRow
-// positions is summed by its own lane; a longer row is cut into 32 contiguous pieces (of
-// more than 8 positions each), one per lane, summed by the whole warp afterwards.  K_i and the intra-community weight stay
-// in each lane's registers until the end, then go through a fixed-order block tree into
-// one partial per block; only the Sigma_c atomics depend on timing.
+// positions is summed by its own lane with the pipelined 16-byte reads of the sweep.  A
+// longer row is read by the whole warp: lane i takes the row's aligned 4-entry groups
+// i, i + 32, ..., so one warp load covers 512 contiguous bytes, and the lanes' sums are
+// then combined.  Every sum is an fp32 TwoSum pair (fp64 runs at a small fraction of the
+// fp32 rate on this GPU): per row, per lane across its rows, and in the combinations.
+// Sigma_c receives K_i by one fp64 atomic per distinct label among the warp's rows (runs
+// of equal labels summed by a segmented scan, run ends of one label joined by a warp
+// match); the totals go through a fixed-order block tree into one partial per block.
+// Only the order of the Sigma_c atomics depends on timing.
 
 constexpr int kModThreads = 256;
-constexpr int kModMaxBlocks = 152 * 3;  // one wave at 3 CTAs per SM (78 registers)
-constexpr int kModShortRow = 256;
+constexpr int kModMaxBlocks = 152 * 3;  // one wave at 3 CTAs per SM
+constexpr int kModShortRow = 64;
 
-// Positions [b, e) of a row into acc: the pipelined 16-byte reads of the sweep when both
-// arrays start on a 16-byte boundary (VEC), else one entry at a time.
+// (hi, lo) += (bh, bl), hi updated by TwoSum
+__device__ __forceinline__ void two_sum_pair(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bh - bb);
+  hi = s;
+  lo = lo + (bl + err);
+}
+
+// Lanes <= lane
+__device__ __forceinline__ unsigned lanes_upto(int lane) { return 0xffffffffu >> (31 - lane); }
+
+// Positions [b, e) of a row into acc by one lane: the pipelined 16-byte reads of the sweep
+// when both arrays start on a 16-byte boundary (VEC), else one entry at a time.
 template <bool WT, bool VEC>
 __device__ __forceinline__ void mod_range(ModAcc& acc, const int32_t* __restrict__ idx,
                                           const float* __restrict__ wts,
@@ -260,16 +277,93 @@ __device__ __forceinline__ void mod_range(ModAcc& acc, const int32_t* __restrict
   }
 }
 
+// One entry-group of a warp-read row: positions 4g .. 4g+3 that lie in [rb, re) (and
+// below m) into acc.
+template <bool WT>
+__device__ __forceinline__ void mod_group(ModAcc& acc, const int32_t* __restrict__ idx,
+                                          const float* __restrict__ wts,
+                                          const int32_t* __restrict__ labels, int64_t m,
+                                          int64_t g, int64_t rb, int64_t re) {
+  const int64_t p = g << 2;
+  int j[4];
+  float x[4];
+  if (p + 4 <= m) {
+    const int4 X = __ldg(reinterpret_cast<const int4*>(idx) + g);
+    const float4 W = WT ? __ldg(reinterpret_cast<const float4*>(wts) + g)
+                        : make_float4(1.f, 1.f, 1.f, 1.f);
+    j[0] = X.x; j[1] = X.y; j[2] = X.z; j[3] = X.w;
+    x[0] = W.x; x[1] = W.y; x[2] = W.z; x[3] = W.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      j[u] = p + u < m ? __ldg(idx + p + u) : 0;
+      x[u] = p + u < m ? (WT ? __ldg(wts + p + u) : 1.f) : 0.f;
+    }
+  }
+  int c[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool use = p + u >= rb && p + u < re && x[u] > 0.f;
+    c[u] = use ? __ldg(labels + j[u]) : -1;
+    x[u] = use ? x[u] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (x[u] > 0.f) acc.add(c[u], x[u]);
+}
+
+// Positions [rb, re) of one row, read by the whole warp into each lane's acc.
+template <bool WT, bool VEC>
+__device__ __forceinline__ void mod_row_warp(ModAcc& acc, const int32_t* __restrict__ idx,
+                                             const float* __restrict__ wts,
+                                             const int32_t* __restrict__ labels, int64_t m,
+                                             int64_t rb, int64_t re) {
+  const int lane = threadIdx.x & 31;
+  if constexpr (VEC) {
+    const int64_t g1 = (re + 3) >> 2;
+    // two groups per lane in flight
+    int64_t g = (rb >> 2) + lane;
+    for (; g + 32 < g1; g += 64) {
+      ModAcc a2{0.f, 0.f, 0.f, 0.f, acc.cv};
+      mod_group<WT>(acc, idx, wts, labels, m, g, rb, re);
+      mod_group<WT>(a2, idx, wts, labels, m, g + 32, rb, re);
+      two_sum_pair(acc.kh, acc.kl, a2.kh, a2.kl);
+      two_sum_pair(acc.ih, acc.il, a2.ih, a2.il);
+    }
+    if (g < g1) mod_group<WT>(acc, idx, wts, labels, m, g, rb, re);
+  } else {
+    for (int64_t p = rb + lane; p < re; p += 32) {
+      const float x = WT ? __ldg(wts + p) : 1.f;
+      if (x > 0.f) acc.add(__ldg(labels + __ldg(idx + p)), x);
+    }
+  }
+}
+
+// Sums of both pairs of acc over the warp (every lane gets them); the two chains are
+// interleaved so their latencies overlap
+__device__ __forceinline__ void warp_acc_sum(ModAcc& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float kh = __shfl_xor_sync(kFullMask, a.kh, o);
+    const float kl = __shfl_xor_sync(kFullMask, a.kl, o);
+    const float ih = __shfl_xor_sync(kFullMask, a.ih, o);
+    const float il = __shfl_xor_sync(kFullMask, a.il, o);
+    two_sum_pair(a.kh, a.kl, kh, kl);
+    two_sum_pair(a.ih, a.il, ih, il);
+  }
+}
+
 template <bool WT, bool VEC>
 __global__ void __launch_bounds__(kModThreads, 3) modularity_rows_kernel(
     const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
     const float* __restrict__ wts, int64_t m, const int32_t* __restrict__ labels, int32_t n,
     double* sigma_c, double* part_k, double* part_in) {
   __shared__ double s_k[kModThreads], s_in[kModThreads];
+  __shared__ float s_h[kModThreads], s_l[kModThreads];
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t ntiles = ((int64_t)n + 31) >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (kModThreads / 32);
-  double tot_k = 0.0, tot_in = 0.0;
+  float tkh = 0.f, tkl = 0.f, tih = 0.f, til = 0.f;  // the lane's totals
   for (int64_t t = (int64_t)blockIdx.x * (kModThreads / 32) + (tid >> 5); t < ntiles;
        t += nwarps) {
     const int64_t v = t * 32 + lane;
@@ -284,39 +378,48 @@ __global__ void __launch_bounds__(kModThreads, 3) modularity_rows_kernel(
     ModAcc acc{0.f, 0.f, 0.f, 0.f, cv};
     const bool longrow = e - b > kModShortRow;
     if (own && !longrow) mod_range<WT, VEC>(acc, idx, wts, labels, m, (int)v, b, e);
-    double kv = acc.k(), in = acc.in();
     for (unsigned lm = __ballot_sync(kFullMask, longrow); lm; lm &= lm - 1) {
       const int src = __ffs(lm) - 1;
-      const int64_t rb = __shfl_sync(kFullMask, b, src);
-      const int64_t d = __shfl_sync(kFullMask, e, src) - rb;
       ModAcc pa{0.f, 0.f, 0.f, 0.f, __shfl_sync(kFullMask, cv, src)};
-      mod_range<WT, VEC>(pa, idx, wts, labels, m, (int)(t * 32 + src), rb + (lane * d) / 32,
-                         rb + ((lane + 1) * d) / 32);
-      double sk = pa.k(), si = pa.in();
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sk += __shfl_xor_sync(kFullMask, sk, o);
-        si += __shfl_xor_sync(kFullMask, si, o);
-      }
-      if (lane == src) {
-        kv = sk;
-        in = si;
-      }
+      mod_row_warp<WT, VEC>(pa, idx, wts, labels, m, __shfl_sync(kFullMask, b, src),
+                            __shfl_sync(kFullMask, e, src));
+      warp_acc_sum(pa);
+      if (lane == src) acc = pa;
     }
-    tot_k += kv;
-    tot_in += in;
-    s_k[tid] = kv;
+    two_sum_pair(tkh, tkl, acc.kh, acc.kl);
+    two_sum_pair(tih, til, acc.ih, acc.il);
+    // Sigma_c: K_i summed over each run of equal labels among the warp's rows
+    float kh = acc.kh, kl = acc.kl;
+    const int cp = __shfl_up_sync(kFullMask, cv, 1);
+    const unsigned heads = __ballot_sync(kFullMask, lane == 0 || cp != cv);
+    const int run0 = 31 - __clz(heads & lanes_upto(lane));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const float yh = __shfl_up_sync(kFullMask, kh, d);
+      const float yl = __shfl_up_sync(kFullMask, kl, d);
+      if (lane - d >= run0) two_sum_pair(kh, kl, yh, yl);
+    }
+    // run ends of the same label (runs apart in the warp) join before the atomic: a large
+    // community met in several runs costs one atomic on its hot address, not several
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    const bool put = own && tail && (kh != 0.f || kl != 0.f);
+    const unsigned grp = __match_any_sync(kFullMask, put ? cv : -(lane + 2));
+    if (put && __popc(grp) > 1) {
+      s_h[tid] = kh;
+      s_l[tid] = kl;
+    }
     __syncwarp();
-    const unsigned grp = __match_any_sync(kFullMask, own ? cv : -(lane + 2));
-    if (own && lane == __ffs(grp) - 1) {
-      double sum = 0.0;
-      for (unsigned g = grp; g; g &= g - 1) sum += s_k[(tid & ~31) + __ffs(g) - 1];
-      if (sum != 0.0) atomicAdd(sigma_c + cv, sum);
+    if (put && lane == __ffs(grp) - 1) {
+      for (unsigned g = grp & (grp - 1); g; g &= g - 1) {
+        const int q = (tid & ~31) + __ffs(g) - 1;
+        two_sum_pair(kh, kl, s_h[q], s_l[q]);
+      }
+      atomicAdd(sigma_c + cv, (double)kh + (double)kl);
     }
     __syncwarp();
   }
-  s_k[tid] = tot_k;
-  s_in[tid] = tot_in;
+  s_k[tid] = (double)tkh + (double)tkl;
+  s_in[tid] = (double)tih + (double)til;
   __syncthreads();
   for (int h = kModThreads / 2; h > 0; h >>= 1) {
     if (tid < h) {

@@ -207,6 +207,31 @@ def test_modularity_matches_oracle(lpa):
             assert q_close(q, oracle.modularity(g.offsets, g.indices, g.weights, labels))
 
 
+# The standalone pass splits each 256-vertex tile's positions evenly over its warps, so
+# rows are cut between warps and steps; a hub spans many warps, runs of isolated vertices
+# leave empty rows, and label runs of every length meet the per-run Sigma_c atomics.
+@pytest.mark.parametrize("case", ["hubs_fractional", "sparse_integer", "unit"])
+def test_standalone_modularity_cut_rows_match_oracle(lpa, case):
+    if case == "hubs_fractional":
+        g = synth.random_graph(20000, 12, seed=5, wmax=8, power=2.1,
+                               hubs=[(3, 19000), (700, 5000), (701, 4000), (19999, 9000)],
+                               self_loops=0.02, zero_weights=0.03)
+        g.weights = (g.weights.astype(np.float64) * 0.37 + 0.011 * (g.weights > 0)).astype(
+            np.float32)
+    elif case == "sparse_integer":
+        g = synth.random_graph(30000, 0.6, seed=6, wmax=5, self_loops=0.01)
+    else:
+        g = synth.random_graph(9000, 40, seed=7, power=2.1, hubs=[(100, 8000)])
+    off, idx, w = to_dev(g)
+    rng = np.random.default_rng(11)
+    n = g.n
+    for labels in (np.arange(n), np.zeros(n), np.arange(n) // 7, np.arange(n) % 2,
+                   rng.integers(0, max(1, n // 300), n), np.repeat(rng.integers(0, n, n // 50 + 1), 50)[:n]):
+        labels = np.ascontiguousarray(labels.astype(np.int32))
+        q = lpa.modularity(off, idx, w, torch.from_numpy(labels).cuda())
+        assert q_close(q, oracle.modularity(g.offsets, g.indices, g.weights, labels)), case
+
+
 def test_validation_rejects_bad_input(lpa):
     g = synth.random_graph(500, 6, seed=9, wmax=4)
     off, idx, w = to_dev(g)
@@ -306,10 +331,10 @@ def test_convergence_test_is_strict_on_the_device(lpa):
         assert np.array_equal(labels.cpu().numpy(), ref["labels"])
 
 
-# The plan packs integer weights into the index words of its sliced copy when they fit the
-# bits the indices leave free (n = 3000: 12 index bits, so weights below 2^20) and reads
-# fp32 weights otherwise; both must give the oracle's bits.  Weights stay symmetric: each
-# is an elementwise map of an integer weight in 1..8.
+# Weights of every magnitude the sketch sums meet: integers up to about 2^20 (fp32 sums
+# of a row stay exact), just above, and fractional ones (sums round, so the leaf order
+# decides the bits).  Weights stay symmetric: each is an elementwise map of an integer
+# weight in 1..8.
 @pytest.mark.parametrize("weights", ["packed_max", "just_over", "fractional"])
 @pytest.mark.parametrize("mode", ["mg", "bm"])
 def test_weight_formats_match_oracle(lpa, weights, mode):
