@@ -56,8 +56,8 @@ def metric_name(args) -> str:
 # (dram__bytes_read.sum + dram__bytes_write.sum, each kernel launched alone with cold
 # caches) on the workload named below, and the hash of the sweep kernel source it was
 # taken with.  If the source changes, traffic is reported as null until a new capture.
-SWEEP_TRAFFIC = {"src_sha256": "e936b074759fb3a6fcb1ceef6f3959ce2f529c3efdd94ad68251e13e8ff43202", "workload": "lfr26",
-                 "bytes_per_launch": 31384872960}
+SWEEP_TRAFFIC = {"src_sha256": "5a3ef23f9f502d6343449873b580e852602cb58da451c8222d5b32cc21fbe5d7", "workload": "lfr26",
+                 "bytes_per_launch": 31440760064}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "

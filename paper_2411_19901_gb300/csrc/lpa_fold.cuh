@@ -30,15 +30,18 @@ struct MGSketch {
     em = (K == 32) ? 0xffffffffu : ((1u << K) - 1u);
   }
 
-  // (c, w) into the lowest free slot; em must be non-zero
+  // (c, w) into the lowest free slot; em must be non-zero.  The slot is chosen by testing
+  // bits of the one-hot lowest free bit, not by comparing slot numbers: fewer
+  // instructions on the integer ALU pipe, which bounds the sweep.
   __device__ __forceinline__ void place(int c, float w) {
-    const int s0 = __ffs(em) - 1;
-    em &= em - 1u;
+    const unsigned oh = em & (0u - em);
+    em ^= oh;
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      key[s] = (s == s0) ? c : key[s];
-      val[s] = (s == s0) ? w : val[s];
-    }
+    for (int s = 0; s < K; ++s)
+      if (oh & (1u << s)) {
+        key[s] = c;
+        val[s] = w;
+      }
   }
 
   // sketchAccumulate with the clamped decrement: add to a matching slot, else fill the
@@ -164,12 +167,13 @@ struct MGLiteral {
 #pragma unroll
     for (int s = 0; s < K; ++s) em |= (val[s] == 0.f ? 1u : 0u) << s;
     if (em != 0u) {
-      const int s0 = __ffs(em) - 1;
+      const unsigned oh = em & (0u - em);  // the lowest slot of value 0, one-hot
 #pragma unroll
-      for (int s = 0; s < K; ++s) {
-        key[s] = (s == s0) ? c : key[s];
-        val[s] = (s == s0) ? w : val[s];
-      }
+      for (int s = 0; s < K; ++s)
+        if (oh & (1u << s)) {
+          key[s] = c;
+          val[s] = w;
+        }
     } else {
 #pragma unroll
       for (int s = 0; s < K; ++s) val[s] = val[s] - w;
