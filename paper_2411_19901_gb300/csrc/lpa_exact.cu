@@ -1,24 +1,35 @@
 // lpa_exact.cu -- the exact label choice (Eq. 3), the quality baseline of the paper's
 // comparison (the nu-LPA per-vertex hashtable of Fig. 1).
 //
-// Chunk CTAs take runs of consecutive vertices whose rows fit the shared-memory stage:
-// the CTA stages (C_prev[j], w) edge-parallel, then each thread builds its vertex's
-// open-addressing table (capacity = largest power of two <= 2d, linear probing) in
-// shared memory and takes the argmax, ties to the smallest label.  Hub CTAs (rows longer
-// than a chunk) build the table in a global O(E) workspace with atomics.  Sums are exact
-// for integer-valued weights, so the result does not depend on the atomic order.
+// Every vertex gets an open-addressing table (capacity = largest power of two <= 2d,
+// linear probing) of its neighbours' labels and their summed weights; the choice is the
+// heaviest label, ties to the smallest.  Two kernels:
+//  * chunk CTAs take runs of consecutive vertices whose rows fit the shared-memory stage.
+//    The CTA stages (C_prev[j], w) entry-parallel, then inserts entry-parallel: a warp
+//    takes 32 consecutive positions, sums runs of equal (row, label) with a segmented
+//    scan across its lanes, and the run's last lane adds the sum with one shared-memory
+//    atomic -- so rows of every length share the CTA's threads evenly, and a row whose
+//    neighbours mostly share one label does not pile its atomics onto one slot.  The
+//    argmax is slot-parallel too: (sum, label) packed so that a larger 64-bit value means
+//    a heavier sum, then a smaller label, and reduced per row by a segmented warp
+//    maximum and one shared atomic maximum per run.
+//  * hub CTAs (rows longer than a chunk) build the row's table in shared memory when it
+//    fits (kHubSmemSlots) and in a global O(E) workspace otherwise, with the same
+//    warp-aggregated inserts.
+// Sums are exact for integer-valued weights, so the result does not depend on the
+// atomic order.
 #include "lpa_internal.cuh"
 
 namespace lpa {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Largest hub table kept in shared memory: 8192 slots (64 KB), three hub CTAs per SM.
+constexpr int kHubSmemSlots = 8192;
 
 __device__ __forceinline__ int commit(int c, int old, int pick_less) {
   return (c >= 0 && c != old && (!pick_less || c < old)) ? c : old;
 }
-
-// ------------------------------------------------------------------ exact mode
 
 __device__ __forceinline__ unsigned table_hash(int c, int lg) {
   return ((unsigned)c * 2654435761u) >> (32 - lg);
@@ -28,12 +39,63 @@ __device__ __forceinline__ bool better_kv(float v, int k, float bv, int bk) {
   return (v > bv) || (v == bv && v > 0.f && k < bk);
 }
 
+// log2 of a row's table capacity: the largest power of two <= 2d (> d)
+__device__ __forceinline__ int table_lg(int64_t d) {
+  return 63 - __clzll(2 * d);
+}
+
+// Runs of equal key among the warp's lanes (all 32 lanes call it): w becomes the sum of
+// the run's weights up to this lane; returns true on the run's last lane.
+template <class K>
+__device__ __forceinline__ bool run_sum(K key, float& w) {
+  const int lane = threadIdx.x & 31;
+  const K kp = __shfl_up_sync(kFull, key, 1);
+  const unsigned heads = __ballot_sync(kFull, lane == 0 || kp != key);
+  const int run0 = 31 - __clz(heads & (kFull >> (31 - lane)));
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float y = __shfl_up_sync(kFull, w, d);
+    if (lane - d >= run0) w += y;
+  }
+  return lane == 31 || ((heads >> (lane + 1)) & 1u);
+}
+
+// Add w to label c's slot of the table (tk, tv) of capacity 2^lg: linear probing from
+// the label's hash, claiming an empty slot by compare-and-swap.  The table never fills
+// (a row has fewer distinct labels than slots), so the probe ends.
+__device__ __forceinline__ void table_add(int* tk, float* tv, int lg, int c, float w) {
+  const unsigned mask = (1u << lg) - 1u;
+  unsigned s = table_hash(c, lg);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(tk + s, -1, c);
+    if (old == -1 || old == c) {
+      atomicAdd(tv + s, w);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+}
+
+// (sum, label) packed so that the larger value is the heavier sum, then the smaller label
+// (sums are positive, so their bit patterns order like the values); 0 = no label
+__device__ __forceinline__ unsigned long long pack_kv(float v, int k) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | (0xffffffffu - (unsigned)k);
+}
+__device__ __forceinline__ int unpack_label(unsigned long long p) {
+  return (p >> 32) != 0 ? (int)(0xffffffffu - (unsigned)p) : -1;
+}
+
+// Hub CTA: one long row, its table in shared memory (capacity <= kHubSmemSlots) or in
+// the global workspace.
 template <bool WT>
-__device__ void hub_exact(const SweepArgs& a, int h) {
+__global__ void __launch_bounds__(kThreads) sweep_exact_hub_kernel(SweepArgs a) {
+  if (a.done != nullptr && *a.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_bv[kThreads / 32];
   __shared__ int s_bk[kThreads / 32];
-  const int tid = threadIdx.x;
   __shared__ int s_changed;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h = blockIdx.x;
   const int v = a.hubs[h];
   const int64_t base = a.off[v];
   const int64_t d = a.off[v + 1] - base;
@@ -41,30 +103,31 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
     if (tid == 0) a.c_next[v] = a.c_prev[v];  // not swept: keep the label
     return;
   }
-  int lg = 1;
-  while (((int64_t)1 << (lg + 1)) <= 2 * d) ++lg;
-  const int64_t cap = (int64_t)1 << lg;  // largest power of two <= 2d (> d)
-  int* tk = a.tab_keys + a.hub_tab[h];
-  float* tv = a.tab_vals + a.hub_tab[h];
+  const int lg = table_lg(d);
+  const int64_t cap = (int64_t)1 << lg;
+  const bool in_smem = cap <= kHubSmemSlots;
+  int* tk = in_smem ? reinterpret_cast<int*>(smem) : a.tab_keys + a.hub_tab[h];
+  float* tv = in_smem ? reinterpret_cast<float*>(smem + sizeof(int) * kHubSmemSlots)
+                      : a.tab_vals + a.hub_tab[h];
   for (int64_t s = tid; s < cap; s += kThreads) {
     tk[s] = -1;
     tv[s] = 0.f;
   }
   __syncthreads();
-  for (int64_t q = base + tid; q < base + d; q += kThreads) {
-    const int j = __ldg(a.idx + q);
-    const float w = WT ? __ldg(a.w + q) : 1.f;
-    if (j == v || !(w > 0.f)) continue;
-    const int c = __ldg(a.c_prev + j);
-    unsigned s = table_hash(c, lg);
-    for (int64_t probe = 0; probe < cap; ++probe) {
-      const int old = atomicCAS(tk + s, -1, c);
-      if (old == -1 || old == c) {
-        atomicAdd(tv + s, w);
-        break;
+  // entries 32 at a time per warp; runs of equal labels are summed first
+  for (int64_t q0 = base + 32 * warp; q0 < base + d; q0 += kThreads) {
+    const int64_t q = q0 + lane;
+    int c = -1;
+    float w = 0.f;
+    if (q < base + d) {
+      const int j = __ldg(a.idx + q);
+      const float x = WT ? __ldg(a.w + q) : 1.f;
+      if (j != v && x > 0.f) {
+        c = __ldg(a.c_prev + j);
+        w = x;
       }
-      s = (s + 1) & (unsigned)(cap - 1);
     }
+    if (run_sum(c, w) && c >= 0) table_add(tk, tv, lg, c, w);
   }
   __syncthreads();
   float bv = 0.f;
@@ -86,9 +149,9 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
       bk = ok;
     }
   }
-  if ((tid & 31) == 0) {
-    s_bv[tid >> 5] = bv;
-    s_bk[tid >> 5] = bk;
+  if (lane == 0) {
+    s_bv[warp] = bv;
+    s_bk[warp] = bk;
   }
   __syncthreads();
   if (tid == 0) {
@@ -112,25 +175,42 @@ __device__ void hub_exact(const SweepArgs& a, int h) {
   }
 }
 
+// Chunk CTA: a run of consecutive vertices whose rows fit the stage (kChunkCapExact).
 template <bool WT>
-__device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) {
+__global__ void __launch_bounds__(kThreads) sweep_exact_chunk_kernel(SweepArgs a) {
+  if (a.done != nullptr && *a.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
   int* s_lab = reinterpret_cast<int*>(smem);
   float* s_w = reinterpret_cast<float*>(s_lab + kChunkCapExact);
   int* s_tk = reinterpret_cast<int*>(s_w + (WT ? kChunkCapExact : 0));
   float* s_tv = reinterpret_cast<float*>(s_tk + 2 * kChunkCapExact);
   __shared__ int s_start[kThreads + 1];
   __shared__ int s_old[kThreads];
-  const int tid = threadIdx.x;
+  __shared__ unsigned char s_act[kThreads];
+  __shared__ unsigned long long s_best[kThreads];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int chunk = blockIdx.x;
   const int v0 = a.chunk_v0[chunk];
   const int nv = a.chunk_v1[chunk] - v0;
   const int64_t base = a.off[v0];
   if (tid < nv) {
     s_start[tid] = (int)(a.off[v0 + tid] - base);
     s_old[tid] = a.c_prev[v0 + tid];
+    s_act[tid] = (a.act_in == nullptr || a.act_in[v0 + tid] != 0) &&
+                 (a.gid == nullptr || !a.gdone[a.gid[v0 + tid]]);
+    s_best[tid] = 0ull;
   }
   if (tid == 0) s_start[nv] = (int)(a.off[v0 + nv] - base);
   __syncthreads();
   const int ne = s_start[nv];
+  // the row holding chunk position q: the last row starting at or before it
+  auto row_of = [&](int q) {
+    int r = 0;
+#pragma unroll
+    for (int st = kThreads / 2; st > 0; st >>= 1)
+      if (r + st < nv && s_start[r + st] <= q) r += st;
+    return r;
+  };
   for (int q = tid; q < ne; q += kThreads) {
     const int j = __ldg(a.idx + base + q);
     const float w = WT ? __ldg(a.w + base + q) : 1.f;
@@ -139,41 +219,58 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
     s_lab[q] = (self || !(w > 0.f)) ? -1 : __ldg(a.c_prev + j);
     if (WT) s_w[q] = w;
   }
+  for (int s = tid; s < 2 * ne; s += kThreads) {
+    s_tk[s] = -1;
+    s_tv[s] = 0.f;
+  }
+  __syncthreads();
+  // inserts: 32 consecutive positions per warp step, runs of equal (row, label) summed
+  for (int q0 = 32 * warp; q0 < ne; q0 += kThreads) {
+    const int q = q0 + lane;
+    int c = -1, r = 0;
+    float w = 0.f;
+    if (q < ne) {
+      c = s_lab[q];
+      if (c >= 0) {
+        r = row_of(q);
+        if (s_act[r]) w = WT ? s_w[q] : 1.f;
+        else c = -1;
+      }
+    }
+    const unsigned long long key =
+        c >= 0 ? ((unsigned long long)(unsigned)r << 32) | (unsigned)c : ~0ull;
+    if (run_sum(key, w) && c >= 0) {
+      const int b = s_start[r];
+      table_add(s_tk + 2 * b, s_tv + 2 * b, table_lg(s_start[r + 1] - b), c, w);
+    }
+  }
+  __syncthreads();
+  // argmax per row: slot-parallel, runs of one row reduced by a segmented warp maximum
+  for (int i0 = 32 * warp; i0 < 2 * ne; i0 += kThreads) {
+    const int i = i0 + lane;
+    int r = nv;  // past the last row: no slot
+    unsigned long long pk = 0ull;
+    if (i < 2 * ne) {
+      r = row_of(i >> 1);  // row r's table lies in slots [2 start_r, 2 start_{r+1})
+      const int k = s_tk[i];
+      if (k >= 0) pk = pack_kv(s_tv[i], k);
+    }
+    const int rp = __shfl_up_sync(kFull, r, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || rp != r);
+    const int run0 = 31 - __clz(heads & (kFull >> (31 - lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, pk, d);
+      if (lane - d >= run0 && y > pk) pk = y;
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && pk != 0ull) atomicMax(s_best + r, pk);
+  }
   __syncthreads();
   int changed = 0;
-  int nl = 0;
-  const bool act = tid < nv && (a.act_in == nullptr || a.act_in[v0 + tid] != 0) &&
-                   (a.gid == nullptr || !a.gdone[a.gid[v0 + tid]]);
   if (tid < nv) {
-    const int b = s_start[tid], d = act ? s_start[tid + 1] - b : 0;
-    int best = -1;
-    if (d > 0) {
-      int lg = 1;
-      while ((1 << (lg + 1)) <= 2 * d) ++lg;
-      const int cap = 1 << lg;
-      int* tk = s_tk + 2 * b;
-      float* tv = s_tv + 2 * b;
-      for (int s = 0; s < cap; ++s) {
-        tk[s] = -1;
-        tv[s] = 0.f;
-      }
-      for (int q = b; q < b + d; ++q) {
-        const int c = s_lab[q];
-        if (c < 0) continue;
-        const float w = WT ? s_w[q] : 1.f;
-        unsigned s = table_hash(c, lg);
-        while (tk[s] != -1 && tk[s] != c) s = (s + 1) & (unsigned)(cap - 1);
-        tk[s] = c;
-        tv[s] = tv[s] + w;
-      }
-      float bv = 0.f;
-      for (int s = 0; s < cap; ++s)
-        if (tk[s] >= 0 && better_kv(tv[s], tk[s], bv, best)) {
-          bv = tv[s];
-          best = tk[s];
-        }
-    }
-    nl = commit(best, s_old[tid], a.gpl != nullptr ? a.gpl[a.gid[v0 + tid]] : a.pick_less);
+    const int nl = commit(unpack_label(s_best[tid]), s_old[tid],
+                          a.gpl != nullptr ? a.gpl[a.gid[v0 + tid]] : a.pick_less);
     changed = nl != s_old[tid];
     a.c_next[v0 + tid] = nl;
     if (changed && a.gdn != nullptr) atomicAdd(a.gdn + a.gid[v0 + tid], 1u);
@@ -194,16 +291,6 @@ __device__ void chunk_exact(const SweepArgs& a, int chunk, unsigned char* smem) 
   }
 }
 
-template <bool WT>
-__global__ void __launch_bounds__(kThreads) sweep_exact_kernel(SweepArgs a) {
-  if (a.done != nullptr && *a.done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  if ((int)blockIdx.x < a.nhubs)
-    hub_exact<WT>(a, (int)blockIdx.x);
-  else
-    chunk_exact<WT>(a, (int)blockIdx.x - a.nhubs, smem);
-}
-
 }  // namespace
 
 size_t exact_smem_bytes(bool weighted) {
@@ -211,14 +298,24 @@ size_t exact_smem_bytes(bool weighted) {
 }
 
 cudaError_t launch_sweep_exact(bool weighted, const SweepArgs& a, cudaStream_t s) {
-  const size_t smem = exact_smem_bytes(weighted);
-  auto kern = weighted ? sweep_exact_kernel<true> : sweep_exact_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)(a.nhubs + a.nchunks);
-  if (grid == 0) return cudaSuccess;
-  kern<<<grid, kThreads, smem, s>>>(a);
-  count_launch();
+  if (a.nhubs > 0) {
+    const size_t smem = (size_t)kHubSmemSlots * (sizeof(int) + sizeof(float));
+    auto kern = weighted ? sweep_exact_hub_kernel<true> : sweep_exact_hub_kernel<false>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)a.nhubs, kThreads, smem, s>>>(a);
+    count_launch();
+  }
+  if (a.nchunks > 0) {
+    const size_t smem = exact_smem_bytes(weighted);
+    auto kern = weighted ? sweep_exact_chunk_kernel<true> : sweep_exact_chunk_kernel<false>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)a.nchunks, kThreads, smem, s>>>(a);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 
