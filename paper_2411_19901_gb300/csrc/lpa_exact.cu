@@ -26,6 +26,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 // Largest hub table kept in shared memory: 8192 slots (64 KB), three hub CTAs per SM.
 constexpr int kHubSmemSlots = 8192;
+// Positions a thread loads before it gathers their labels (memory-level parallelism).
+constexpr int kStageBatch = 4;
 
 __device__ __forceinline__ int commit(int c, int old, int pick_less) {
   return (c >= 0 && c != old && (!pick_less || c < old)) ? c : old;
@@ -114,20 +116,34 @@ __global__ void __launch_bounds__(kThreads) sweep_exact_hub_kernel(SweepArgs a) 
     tv[s] = 0.f;
   }
   __syncthreads();
-  // entries 32 at a time per warp; runs of equal labels are summed first
-  for (int64_t q0 = base + 32 * warp; q0 < base + d; q0 += kThreads) {
-    const int64_t q = q0 + lane;
-    int c = -1;
-    float w = 0.f;
-    if (q < base + d) {
-      const int j = __ldg(a.idx + q);
-      const float x = WT ? __ldg(a.w + q) : 1.f;
-      if (j != v && x > 0.f) {
-        c = __ldg(a.c_prev + j);
-        w = x;
-      }
+  // entries 32 at a time per warp, kStageBatch steps loaded and gathered together; runs
+  // of equal labels are summed before their atomic
+  for (int64_t q0 = base + 32 * warp; q0 < base + d; q0 += kStageBatch * kThreads) {
+    int c[kStageBatch];
+    float w[kStageBatch];
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int64_t q = q0 + u * kThreads + lane;
+      c[u] = q < base + d ? __ldg(a.idx + q) : v;
+      w[u] = q < base + d ? (WT ? __ldg(a.w + q) : 1.f) : 0.f;
     }
-    if (run_sum(c, w) && c >= 0) table_add(tk, tv, lg, c, w);
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const bool use = c[u] != v && w[u] > 0.f;
+      c[u] = use ? __ldg(a.c_prev + c[u]) : -1;
+      w[u] = use ? w[u] : 0.f;
+    }
+#pragma unroll 1
+    for (int u = 0; u < kStageBatch; ++u) {
+      int cu = c[0];
+      float wu = w[0];
+#pragma unroll
+      for (int t = 0; t + 1 < kStageBatch; ++t) {
+        c[t] = c[t + 1];
+        w[t] = w[t + 1];
+      }
+      if (run_sum(cu, wu) && cu >= 0) table_add(tk, tv, lg, cu, wu);
+    }
   }
   __syncthreads();
   float bv = 0.f;
@@ -188,6 +204,8 @@ __global__ void __launch_bounds__(kThreads) sweep_exact_chunk_kernel(SweepArgs a
   __shared__ int s_old[kThreads];
   __shared__ unsigned char s_act[kThreads];
   __shared__ unsigned long long s_best[kThreads];
+  __shared__ unsigned char s_row[kChunkCapExact];  // the row of each chunk position
+  __shared__ int s_wmax[kThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int chunk = blockIdx.x;
   const int v0 = a.chunk_v0[chunk];
@@ -203,25 +221,62 @@ __global__ void __launch_bounds__(kThreads) sweep_exact_chunk_kernel(SweepArgs a
   if (tid == 0) s_start[nv] = (int)(a.off[v0 + nv] - base);
   __syncthreads();
   const int ne = s_start[nv];
-  // the row holding chunk position q: the last row starting at or before it
-  auto row_of = [&](int q) {
-    int r = 0;
+  // stage kStageBatch positions per thread at a time: their loads, then their gathers
+  for (int q0 = tid; q0 < ne; q0 += kStageBatch * kThreads) {
+    int j[kStageBatch];
+    float w[kStageBatch];
 #pragma unroll
-    for (int st = kThreads / 2; st > 0; st >>= 1)
-      if (r + st < nv && s_start[r + st] <= q) r += st;
-    return r;
-  };
-  for (int q = tid; q < ne; q += kThreads) {
-    const int j = __ldg(a.idx + base + q);
-    const float w = WT ? __ldg(a.w + base + q) : 1.f;
-    const unsigned r = (unsigned)(j - v0);
-    const bool self = r < (unsigned)nv && s_start[r] <= q && q < s_start[r + 1];
-    s_lab[q] = (self || !(w > 0.f)) ? -1 : __ldg(a.c_prev + j);
-    if (WT) s_w[q] = w;
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int q = q0 + u * kThreads;
+      j[u] = q < ne ? __ldg(a.idx + base + q) : -1;
+      w[u] = q < ne ? (WT ? __ldg(a.w + base + q) : 1.f) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int q = q0 + u * kThreads;
+      if (q < ne) {
+        const unsigned r = (unsigned)(j[u] - v0);
+        const bool self = r < (unsigned)nv && s_start[r] <= q && q < s_start[r + 1];
+        s_lab[q] = (self || !(w[u] > 0.f)) ? -1 : __ldg(a.c_prev + j[u]);
+        if (WT) s_w[q] = w[u];
+      }
+    }
   }
   for (int s = tid; s < 2 * ne; s += kThreads) {
     s_tk[s] = -1;
     s_tv[s] = 0.f;
+  }
+  // the row of every position: each non-empty row marks its first position, then a
+  // running maximum over the positions (rows are in position order)
+  for (int q = tid; q < ne; q += kThreads) s_row[q] = 0;
+  __syncthreads();
+  if (tid < nv && s_start[tid] < s_start[tid + 1]) s_row[s_start[tid]] = (unsigned char)tid;
+  __syncthreads();
+  {
+    constexpr int kPer = kChunkCapExact / kThreads;  // positions per thread, in a block
+    const int q0 = tid * kPer;
+    int m = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+      if (q0 + u < ne) m = max(m, (int)s_row[q0 + u]);
+    // maximum over the threads below (exclusive): warp scan, then across warps
+    int x = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, d);
+      if (lane >= d) x = max(x, y);
+    }
+    if (lane == 31) s_wmax[warp] = x;
+    __syncthreads();
+    int before = __shfl_up_sync(kFull, x, 1);
+    if (lane == 0) before = 0;
+    for (int w = 0; w < warp; ++w) before = max(before, s_wmax[w]);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+      if (q0 + u < ne) {
+        before = max(before, (int)s_row[q0 + u]);
+        s_row[q0 + u] = (unsigned char)before;
+      }
   }
   __syncthreads();
   // inserts: 32 consecutive positions per warp step, runs of equal (row, label) summed
@@ -232,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) sweep_exact_chunk_kernel(SweepArgs a
     if (q < ne) {
       c = s_lab[q];
       if (c >= 0) {
-        r = row_of(q);
+        r = s_row[q];
         if (s_act[r]) w = WT ? s_w[q] : 1.f;
         else c = -1;
       }
@@ -251,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) sweep_exact_chunk_kernel(SweepArgs a
     int r = nv;  // past the last row: no slot
     unsigned long long pk = 0ull;
     if (i < 2 * ne) {
-      r = row_of(i >> 1);  // row r's table lies in slots [2 start_r, 2 start_{r+1})
+      r = s_row[i >> 1];  // row r's table lies in slots [2 start_r, 2 start_{r+1})
       const int k = s_tk[i];
       if (k >= 0) pk = pack_kv(s_tv[i], k);
     }
