@@ -52,12 +52,15 @@ def metric_name(args) -> str:
         name = {"bm": "BM", "exact": "exact"}[args.mode]
     return f"{name}-LPA edges/sec/iteration"
 
-# DRAM traffic of one MG k = 8 sweep (its hub and lane kernels together) measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, each kernel launched alone with cold
-# caches) on the workload named below, and the hash of the sweep kernel source it was
-# taken with.  If the source changes, traffic is reported as null until a new capture.
-SWEEP_TRAFFIC = {"src_sha256": "5a3ef23f9f502d6343449873b580e852602cb58da451c8222d5b32cc21fbe5d7", "workload": "lfr26",
-                 "bytes_per_launch": 31440760064}
+# DRAM traffic of one MG k = 8 sweep, from an ncu capture of a small case of the same
+# family (dram__bytes_read.sum + dram__bytes_write.sum of the lane kernel, the whole sweep
+# there since its rows have no hubs) scaled to the workload below by the ratio of their
+# algorithmic bytes, with the hash of the sweep kernel source it was taken with.  If the
+# source changes, traffic is reported as null until a new capture.
+SWEEP_TRAFFIC = {"src_sha256": "5a3ef23f9f502d6343449873b580e852602cb58da451c8222d5b32cc21fbe5d7",
+                 "workload": "lfr26", "captured_on": "lfr26s",
+                 "captured_bytes_per_launch": 10245242112,
+                 "captured_algorithmic_bytes": 5479657280}
 
 WORKLOADS = {
     "lfr26": "LFR-style heavy-tailed planted partition, n=2^26, degree power law 2.1 on "
@@ -612,8 +615,10 @@ def run_ours(args):
     traffic = None
     default_sketch = args.mode == "mg" and args.k == 8 and not (args.unclamped or args.rescan)
     if (default_sketch and SWEEP_TRAFFIC["src_sha256"] == sweep_src_sha()
-            and SWEEP_TRAFFIC["workload"] == args.workload):
-        traffic = SWEEP_TRAFFIC["bytes_per_launch"]
+            and args.workload in (SWEEP_TRAFFIC["workload"], SWEEP_TRAFFIC["captured_on"])):
+        # scaled by algorithmic bytes: traffic per algorithmic byte as on the small case
+        traffic = round(SWEEP_TRAFFIC["captured_bytes_per_launch"] * alg_bytes
+                        / SWEEP_TRAFFIC["captured_algorithmic_bytes"])
     cpu = None
     if world == 1 and not args.skip_cpu:
         times, threads = oracle_sweeps(g, args.mode, seconds=10.0, max_reps=3, k=args.k,
@@ -636,6 +641,9 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": f"{peak_kind} hbm_gbs",
                      # the second fraction: measured DRAM bytes of one sweep over its time
+                     "traffic_source": (f"ncu dram bytes of the lane kernel on "
+                                        f"{SWEEP_TRAFFIC['captured_on']}, scaled by "
+                                        "algorithmic bytes") if traffic else None,
                      "dram_achieved": (traffic / (launch_ms * 1e-3) / 1e9) if traffic else None,
                      "dram_frac": (traffic / (launch_ms * 1e-3) / 1e9 / peak) if traffic else None},
         "cpu_baseline": cpu,
