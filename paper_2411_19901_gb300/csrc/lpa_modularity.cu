@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(256) modularity_total_kernel(const double* a_p
 //
 // A warp takes a tile of 32 consecutive vertices.  A row of at most kModShortRow
 // positions is summed by its own lane with the pipelined 16-byte reads of the sweep.  A
-// longer row is read by the whole warp: lane i takes the row's aligned 4-entry groups
-// i, i + 32, ..., so one warp load covers 512 contiguous bytes, and the lanes' sums are
-// then combined.  Every sum is an fp32 TwoSum pair (fp64 runs at a small fraction of the
+// longer row is read by the whole warp: lane i folds the i-th of 32 contiguous pieces
+// (cut at 4-entry group boundaries) with the same pipelined reads, and the lanes' sums
+// are then combined.  Every sum is an fp32 TwoSum pair (fp64 runs at a small fraction of the
 // fp32 rate on this GPU): per row, per lane across its rows, and in the combinations.
 // Sigma_c receives K_i by one fp64 atomic per distinct label among the warp's rows (runs
 // of equal labels summed by a segmented scan, run ends of one label joined by a warp
@@ -271,68 +271,6 @@ __device__ __forceinline__ void mod_range(ModAcc& acc, const int32_t* __restrict
     fold_range<ModAcc, WT, false>(acc, idx, wts, labels, m, v, b, e);
   } else {
     for (int64_t p = b; p < e; ++p) {
-      const float x = WT ? __ldg(wts + p) : 1.f;
-      if (x > 0.f) acc.add(__ldg(labels + __ldg(idx + p)), x);
-    }
-  }
-}
-
-// One entry-group of a warp-read row: positions 4g .. 4g+3 that lie in [rb, re) (and
-// below m) into acc.
-template <bool WT>
-__device__ __forceinline__ void mod_group(ModAcc& acc, const int32_t* __restrict__ idx,
-                                          const float* __restrict__ wts,
-                                          const int32_t* __restrict__ labels, int64_t m,
-                                          int64_t g, int64_t rb, int64_t re) {
-  const int64_t p = g << 2;
-  int j[4];
-  float x[4];
-  if (p + 4 <= m) {
-    const int4 X = __ldg(reinterpret_cast<const int4*>(idx) + g);
-    const float4 W = WT ? __ldg(reinterpret_cast<const float4*>(wts) + g)
-                        : make_float4(1.f, 1.f, 1.f, 1.f);
-    j[0] = X.x; j[1] = X.y; j[2] = X.z; j[3] = X.w;
-    x[0] = W.x; x[1] = W.y; x[2] = W.z; x[3] = W.w;
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      j[u] = p + u < m ? __ldg(idx + p + u) : 0;
-      x[u] = p + u < m ? (WT ? __ldg(wts + p + u) : 1.f) : 0.f;
-    }
-  }
-  int c[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const bool use = p + u >= rb && p + u < re && x[u] > 0.f;
-    c[u] = use ? __ldg(labels + j[u]) : -1;
-    x[u] = use ? x[u] : 0.f;
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (x[u] > 0.f) acc.add(c[u], x[u]);
-}
-
-// Positions [rb, re) of one row, read by the whole warp into each lane's acc.
-template <bool WT, bool VEC>
-__device__ __forceinline__ void mod_row_warp(ModAcc& acc, const int32_t* __restrict__ idx,
-                                             const float* __restrict__ wts,
-                                             const int32_t* __restrict__ labels, int64_t m,
-                                             int64_t rb, int64_t re) {
-  const int lane = threadIdx.x & 31;
-  if constexpr (VEC) {
-    const int64_t g1 = (re + 3) >> 2;
-    // two groups per lane in flight
-    int64_t g = (rb >> 2) + lane;
-    for (; g + 32 < g1; g += 64) {
-      ModAcc a2{0.f, 0.f, 0.f, 0.f, acc.cv};
-      mod_group<WT>(acc, idx, wts, labels, m, g, rb, re);
-      mod_group<WT>(a2, idx, wts, labels, m, g + 32, rb, re);
-      two_sum_pair(acc.kh, acc.kl, a2.kh, a2.kl);
-      two_sum_pair(acc.ih, acc.il, a2.ih, a2.il);
-    }
-    if (g < g1) mod_group<WT>(acc, idx, wts, labels, m, g, rb, re);
-  } else {
-    for (int64_t p = rb + lane; p < re; p += 32) {
       const float x = WT ? __ldg(wts + p) : 1.f;
       if (x > 0.f) acc.add(__ldg(labels + __ldg(idx + p)), x);
     }
@@ -381,8 +319,14 @@ __global__ void __launch_bounds__(kModThreads, 3) modularity_rows_kernel(
     for (unsigned lm = __ballot_sync(kFullMask, longrow); lm; lm &= lm - 1) {
       const int src = __ffs(lm) - 1;
       ModAcc pa{0.f, 0.f, 0.f, 0.f, __shfl_sync(kFullMask, cv, src)};
-      mod_row_warp<WT, VEC>(pa, idx, wts, labels, m, __shfl_sync(kFullMask, b, src),
-                            __shfl_sync(kFullMask, e, src));
+      // lane i folds the i-th of 32 contiguous pieces of the row, cut at 4-entry group
+      // boundaries so that only the row's ends are partial groups
+      const int64_t rb = __shfl_sync(kFullMask, b, src), re = __shfl_sync(kFullMask, e, src);
+      const int64_t g0 = rb >> 2, ng = ((re + 3) >> 2) - g0;
+      int64_t pb = (g0 + (lane * ng) / 32) << 2, pe = (g0 + ((lane + 1) * ng) / 32) << 2;
+      pb = pb < rb ? rb : pb;
+      pe = pe > re ? re : pe;
+      mod_range<WT, VEC>(pa, idx, wts, labels, m, (int)(t * 32 + src), pb, pe);
       warp_acc_sum(pa);
       if (lane == src) acc = pa;
     }
