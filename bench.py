@@ -903,6 +903,7 @@ def run_serve(args):
     step_time = 0.0
     inflight_sum = 0
     step_admit, step_plain = [], []  # host ms of steps that admitted requests / did not
+    step_log = []  # (host ms, requests admitted, requests in flight) of every step
     torch.cuda.synchronize(dev)
     start = time.perf_counter()
     clocks.mark("start")
@@ -911,7 +912,7 @@ def run_serve(args):
         if not inflight and nxt < total and arrive[nxt] > now:
             time.sleep(max(0.0, arrive[nxt] - now))
             now = time.perf_counter() - start
-        admitted = False
+        admitted = 0
         while nxt < total and arrive[nxt] <= now:
             ho, hi, hw = host[pick[nxt]]
             do = ho.to(dev, non_blocking=True)
@@ -920,7 +921,7 @@ def run_serve(args):
             out = torch.empty(do.numel() - 1, dtype=torch.int32, device=dev)
             inflight[srv.submit(do, di, dw, out)] = (nxt, out)
             nxt += 1
-            admitted = True
+            admitted += 1
         t_step = time.perf_counter()
         srv.step()
         steps += 1
@@ -928,6 +929,7 @@ def run_serve(args):
         dt_step = time.perf_counter() - t_step
         step_time += dt_step
         (step_admit if admitted else step_plain).append(1e3 * dt_step)
+        step_log.append((1e3 * dt_step, admitted, len(inflight)))
         inflight_sum += len(inflight)
         for tk in srv.drain():
             st = srv.poll(tk)
@@ -990,6 +992,15 @@ def run_serve(args):
                                   "p99": pct(step_admit, 99)},
                     "sweep_only": {"steps": len(step_plain), "mean": mean(step_plain),
                                    "p99": pct(step_plain, 99)}},
+        "slowest_steps": [{"ms": round(ms, 3), "admitted": a, "in_flight": f}
+                          for ms, a, f in sorted(step_log, reverse=True)[:5]],
+        "steps_over_5ms": int(sum(1 for ms, _, _ in step_log if ms > 5.0)),
+        # latency by the number of sweeps a request needed (its steps in the server)
+        "by_iterations": {b: {"requests": int(sel.sum()), "p50_ms": pct(lat[sel], 50),
+                              "p99_ms": pct(lat[sel], 99)}
+                          for b, sel in (("<=10", iters[n_warm:] <= 10),
+                                         ("11-19", (iters[n_warm:] > 10) & (iters[n_warm:] < 20)),
+                                         ("20", iters[n_warm:] >= 20))},
         "in_flight_mean": inflight_sum / max(steps, 1),
         "bit_equal_sampled": equal, "sampled": len(outputs),
         "roofline": None, "cpu_baseline": cpu,
