@@ -57,9 +57,9 @@ def metric_name(args) -> str:
 # there since its rows have no hubs) scaled to the workload below by the ratio of their
 # algorithmic bytes, with the hash of the sweep kernel source it was taken with.  If the
 # source changes, traffic is reported as null until a new capture.
-SWEEP_TRAFFIC = {"src_sha256": "5a3ef23f9f502d6343449873b580e852602cb58da451c8222d5b32cc21fbe5d7",
+SWEEP_TRAFFIC = {"src_sha256": "21c06732b4c919e67beb9c7084dae2c298a2eedb244b24fd57d363b1cb381a7e",
                  "workload": "lfr26", "captured_on": "lfr26s",
-                 "captured_bytes_per_launch": 10245242112,
+                 "captured_bytes_per_launch": 10243403648,
                  "captured_algorithmic_bytes": 5479657280}
 
 WORKLOADS = {

@@ -471,8 +471,7 @@ __global__ void __launch_bounds__(kSortThreads) expand_lanes_kernel(
 
 // Profile of the weights and rows: out[0] stays 1 if every weight is an integer, out[1]
 // gets the largest weight's bits and out[2] the longest row (w null: rows only).  The plan
-// packs integer weights into the index words of its sliced copy when they fit, and
-// refuses rows longer than 2^31 - 1.
+// calls it with w null and refuses rows longer than 2^31 - 1.
 __global__ void weight_profile_kernel(const int64_t* off, const float* w, int32_t n, int64_t m,
                                       unsigned long long* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

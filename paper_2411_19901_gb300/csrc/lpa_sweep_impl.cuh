@@ -27,23 +27,26 @@ __device__ __forceinline__ int commit_label(int c, int old, int pick_less) {
 }
 
 // Levels s >= 32 of the stride-doubling tree for a hub with L > 32 leaves: warp leaders
-// deposit their sketches, thread 0 merges them level by level; thread 0 ends with S[0].
+// deposit their sketches; the merges of one level are independent, so thread t of warp 0
+// merges the pair starting at warp 2·s·t, level by level; thread 0 ends with S[0].
 template <class S>
 __device__ __forceinline__ void cross_warp_tree(S& st, int L, int tid, int* sk, float* sv) {
   const int nw = L / 32;
   if ((tid & 31) == 0 && (tid >> 5) < nw)
     st.store(sk + (tid >> 5) * S::kSlots, sv + (tid >> 5) * S::kSlots);
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 32) {
     for (int s = 1; s < nw; s <<= 1) {
-      for (int w = 0; w + s < nw; w += 2 * s) {
+      const int w = tid * 2 * s;
+      if (w + s < nw) {
         S a;
         a.load(sk + w * S::kSlots, sv + w * S::kSlots);
         a.merge_from(sk + (w + s) * S::kSlots, sv + (w + s) * S::kSlots);
         a.store(sk + w * S::kSlots, sv + w * S::kSlots);
       }
+      __syncwarp();
     }
-    st.load(sk, sv);
+    if (tid == 0) st.load(sk, sv);
   }
 }
 
