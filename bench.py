@@ -665,11 +665,65 @@ def run_ours(args):
         "setup_ms": stats[-1]["setup_ms"],
         "generate_s": gen_s,
     }
+    if world == 1 and default_sketch and args.workload == "lfr26" and not args.no_forms:
+        # the batched and served forms, measured after the headline in the same run on the
+        # freed device (their own warm-up, timed region and clock record each)
+        del ws, d_off, d_idx, d_w, labels, h_lab
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        lpa.lpa_release_memory()
+        line["forms"] = measure_forms(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+FORM_KEYS = {
+    "batched": ("metric", "value", "unit", "ms_per_step", "steps", "warmup",
+                "one_call_per_graph", "e2e", "iterations_max", "iterations_mean",
+                "gpu_launches", "clocks", "generate_s"),
+    "served": ("metric", "p50_ms", "p99_ms", "mean_ms", "max_ms", "throughput_per_s",
+               "by_kind", "one_at_a_time", "bit_equal_sampled", "sampled", "step_ms",
+               "steps_over_5ms", "in_flight_mean", "steps", "warmup", "gpu_launches", "clocks",
+               "generate_s"),
+}
+
+
+def measure_forms(args) -> dict:
+    """Short runs of the batched form (the first 256 graphs of the batched family, 3 timed
+    batches) and of the served form (the full arrival stream and request pool, 4000 timed
+    requests), without their oracle baselines.  A failure is reported in place of the
+    numbers; it never stops the headline line."""
+    import argparse as _ap
+
+    out = {}
+    for form, workload, steps in (("batched", "sbm256", 3), ("served", "serve", 1)):
+        sub = _ap.Namespace(**vars(args))
+        sub.workload, sub.steps, sub.warmup, sub.tune, sub.skip_cpu = workload, steps, 3, False, True
+        t0 = time.perf_counter()
+        try:
+            line = run_batch(sub, emit=False) if form == "batched" else run_serve(sub, emit=False)
+            res = {k: line[k] for k in FORM_KEYS[form] if k in line}
+            res["config"] = line["config"]
+            if form == "batched":
+                res["roofline_frac"] = line["roofline"]["frac"]
+        except Exception as exc:  # noqa: BLE001 -- reported in the line, not raised
+            res = {"error": f"{type(exc).__name__}: {exc}"}
+        res["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[form] = res
+        try:
+            import torch
+
+            import paper_2411_19901_gb300 as lpa
+
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            lpa.lpa_release_memory()
+        except Exception:  # noqa: BLE001
+            pass
+    return out
 
 
 def _gen_member(g):
@@ -685,9 +739,10 @@ def make_batch(count: int):
         return pool.map(_gen_member, range(count), chunksize=4)
 
 
-def run_batch(args):
+def run_batch(args, emit: bool = True):
     """Batched form: one lpa_batch_detect over the whole batch per step, against one
-    lpa_detect_ex per graph.  Unit: graphs per second over the batch."""
+    lpa_detect_ex per graph.  Unit: graphs per second over the batch.  Returns the JSON
+    line (rank 0), printing it when emit."""
     world, rank, local = dist_env()
     t0 = time.perf_counter()
     gs = make_batch(BATCH_COUNT[args.workload])
@@ -801,7 +856,7 @@ def run_batch(args):
     iters = [s["iterations"] for s in stats]
     useful = sum(it * sweep_bytes(g.n, g.m, g.weights is not None) for it, g in zip(iters, gs))
     cpu = None
-    if world == 1:
+    if world == 1 and not args.skip_cpu:
         rate, done, dt, threads = oracle_batch_rate(gs, args.mode, 10.0)
         cpu = {"value": rate, "unit": "graphs/s", "cores": threads, "kind": "oracle",
                "sample": f"full oracle runs of the batch's first {done} graphs, {dt:.1f} s"}
@@ -837,11 +892,13 @@ def run_batch(args):
                    if args.tune else {"chosen": "defaults"}),
         "generate_s": gen_s,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+    return line
 
 
 def _gen_serve(i):
@@ -850,11 +907,12 @@ def _gen_serve(i):
     return synth.rmat(scale=20, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=i - 512)
 
 
-def run_serve(args):
+def run_serve(args, emit: bool = True):
     """Served form: requests arrive by a Poisson process; each step of the host loop
     submits the requests that have arrived (copying their graph to the device), runs one
     lpa_server_step and polls.  Latency = completion (host clock after the step that
-    finished the request) - arrival."""
+    finished the request) - arrival.  Returns the JSON line (rank 0), printing it when
+    emit."""
     import multiprocessing as mp
 
     world, rank, local = dist_env()
@@ -964,7 +1022,7 @@ def run_serve(args):
     def mean(x):
         return float(np.mean(x)) if len(x) else None
     cpu = None
-    if world == 1:
+    if world == 1 and not args.skip_cpu:
         olat, threads = oracle_serve_latencies(gpool, args.mode, 10.0)
         cpu = {"value": float(np.percentile(olat, 99)), "unit": "ms", "cores": threads,
                "kind": "oracle",
@@ -1011,7 +1069,9 @@ def run_serve(args):
                 "note": "latency is end to end: host-to-device copy at arrival included"},
         "gpu_launches": launches, "clocks": clk, "generate_s": gen_s,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def serve_one_at_a_time(lpa, host, gpool, arrive, pick, n_warm, args, stream):
@@ -1059,6 +1119,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true",
                     help="leave out the oracle's cpu_baseline (for ablation tables; the "
                          "default run always reports it)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave out the short batched and served runs that the default "
+                         "workload reports under 'forms'")
     ap.add_argument("--tune", action="store_true",
                     help="time the autotuner's candidates first and run the timed steps with "
                          "its pick (the default launch choices are timed beside it)")
