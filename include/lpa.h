@@ -76,6 +76,17 @@ typedef enum {
  * along the merge tree) and the heaviest, ties to the smallest label, is chosen. */
 #define LPA_MG_UNCLAMPED 0x10u
 #define LPA_RESCAN 0x20u
+/* Record a run's launches as one CUDA graph and launch that (the driver loop of Alg. 1:
+ * every sweep with its on-device stop test, the labels' final copy, the optional
+ * modularity pass and the copies of the results to the host).  A plan keeps the
+ * instantiated graph and replays it on the next lpa_plan_run with the same labels_out,
+ * tol, max_iter and flags (a new combination records a new graph); lpa_detect*,
+ * lpa_batch_detect (its sweeps and per-graph stop tests) record and launch a graph per
+ * call.  Results are the same bits as without the flag.  The graph is recorded on a
+ * stream of the library's own and launched on the caller's stream, so the legacy
+ * default stream works too.  Not with LPA_TIMING (LPA_EINVAL): per-sweep events are not
+ * timed inside a graph.  The server ignores the flag. */
+#define LPA_GRAPH 0x40u
 
 /* Largest max_iter accepted; lpa_stats.changed has this many entries. */
 #define LPA_MAX_ITER 1024
@@ -123,7 +134,8 @@ typedef struct {
   int32_t leaf_max;         /* Lmax: most partial sketches per row, power of two
                                <= 256.  Default 256. */
   uint32_t flags;           /* LPA_VALIDATE | LPA_TIMING | LPA_MODULARITY | LPA_PRUNE |
-                               LPA_MG_UNCLAMPED | LPA_RESCAN.  Default LPA_VALIDATE. */
+                               LPA_MG_UNCLAMPED | LPA_RESCAN | LPA_GRAPH.  Default
+                               LPA_VALIDATE. */
   const int32_t* labels_in; /* device, n labels in [0, n) to start from; NULL = C[i]=i */
   void* stream;             /* cudaStream_t; NULL = legacy default stream */
   void* workspace;          /* device scratch of workspace_bytes bytes, 256-byte

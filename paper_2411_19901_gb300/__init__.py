@@ -5,7 +5,8 @@ The compute path is the CUDA library ``liblpa.so`` (sources in ``csrc/``, C ABI 
 :mod:`.tune` times the launch choices that never change a result.
 """
 from .lpa import (  # noqa: F401
-    LPA_BM, LPA_EXACT, LPA_MG, LPA_MG_UNCLAMPED, LPA_MODULARITY, LPA_PRUNE, LPA_RESCAN,
+    LPA_BM, LPA_EXACT, LPA_GRAPH, LPA_MG, LPA_MG_UNCLAMPED, LPA_MODULARITY, LPA_PRUNE,
+    LPA_RESCAN,
     LPA_TIMING, LPA_VALIDATE, LpaError, Plan, Server, detect,
     lpa_batch_detect, lpa_detect, lpa_detect_ex, lpa_detect_host, lpa_launch_count, lpa_modularity, lpa_modularity_ex,
     lpa_modularity_workspace_size, lpa_options, lpa_options_init, lpa_plan_create,

@@ -283,6 +283,15 @@ struct lpa_plan_s {
   unsigned long long* host_scan = nullptr;
   double* host_q = nullptr;
   unsigned long long* host_cls = nullptr;
+  // LPA_GRAPH: the recorded run (its launches as one CUDA graph), the arguments it was
+  // recorded with, its kernel count, and the library's own stream it is recorded on
+  cudaGraphExec_t gexec = nullptr;
+  const int32_t* g_labels_out = nullptr;
+  double g_tol = 0.0;
+  int32_t g_max_iter = -1;
+  uint32_t g_flags = 0;
+  unsigned long long g_kernels = 0;
+  cudaStream_t rec = nullptr;
 };
 
 namespace {
@@ -350,8 +359,67 @@ cudaError_t launch_one_sweep(const lpa_plan_s* p, const SweepArgs& a) {
   return e;
 }
 
+// LPA_GRAPH: run enqueue(stream) -- stream-ordered launches and copies only, no host
+// synchronisation -- as one CUDA graph launched on the plan's stream.  The graph is
+// recorded on a stream of the plan's own (capture is not possible on the legacy default
+// stream) with the plan's stream field pointing at it meanwhile, instantiated, kept, and
+// launched again while labels_out, tol, max_iter and the flags are those it was recorded
+// with.  Capture-time launch counts are taken back and each launch of the graph adds its
+// kernel count instead.
+template <class F>
+lpa_status run_recorded(lpa_plan_s* p, const int32_t* labels_out, double tol, int32_t max_iter,
+                        F&& enqueue) {
+  cudaStream_t s = p->stream;
+  const bool same = p->gexec && p->g_labels_out == labels_out && p->g_tol == tol &&
+                    p->g_max_iter == max_iter && p->g_flags == p->flags;
+  if (!same) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    if (!p->rec) LPA_CUDA(cudaStreamCreateWithFlags(&p->rec, cudaStreamNonBlocking));
+    LPA_CUDA(cudaStreamBeginCapture(p->rec, cudaStreamCaptureModeThreadLocal));
+    p->stream = p->rec;
+    lpa_status st = enqueue(p->rec);
+    p->stream = s;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->rec, &g);  // ends it after a failure too
+    size_t nodes = 0;
+    unsigned long long kernels = 0;
+    if (st == LPA_OK && ce == cudaSuccess && cudaGraphGetNodes(g, nullptr, &nodes) == cudaSuccess) {
+      std::vector<cudaGraphNode_t> all(nodes);
+      if (nodes > 0 && cudaGraphGetNodes(g, all.data(), &nodes) == cudaSuccess)
+        for (cudaGraphNode_t nd : all) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+        }
+    }
+    g_launches.fetch_sub(kernels, std::memory_order_relaxed);
+    if (st != LPA_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != LPA_OK ? st : fail(LPA_ECUDA, "recording the run: %s", cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      p->gexec = nullptr;
+      return fail(LPA_ECUDA, "instantiating the recorded run: %s", cudaGetErrorString(ie));
+    }
+    p->g_labels_out = labels_out;
+    p->g_tol = tol;
+    p->g_max_iter = max_iter;
+    p->g_flags = p->flags;
+    p->g_kernels = kernels;
+  }
+  LPA_CUDA(cudaGraphLaunch(p->gexec, s));
+  g_launches.fetch_add(p->g_kernels, std::memory_order_relaxed);
+  return LPA_OK;
+}
+
 void destroy_plan(lpa_plan_s* p) {
   if (!p) return;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->rec) cudaStreamDestroy(p->rec);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   if (p->join_ev) cudaEventDestroy(p->join_ev);
@@ -524,6 +592,9 @@ lpa_status plan_create(const int64_t* offsets, const int32_t* indices, const flo
   if (o.leaf_e0 < 1) return fail(LPA_EINVAL, "leaf_e0 = %d must be >= 1", o.leaf_e0);
   if ((o.flags & (LPA_MG_UNCLAMPED | LPA_RESCAN)) && mode != LPA_MG)
     return fail(LPA_EINVAL, "LPA_MG_UNCLAMPED and LPA_RESCAN apply to LPA_MG only");
+  if ((o.flags & LPA_GRAPH) && (o.flags & LPA_TIMING))
+    return fail(LPA_EINVAL, "LPA_GRAPH and LPA_TIMING cannot be combined: per-sweep events are "
+                "not timed inside a graph");
   if (o.leaf_max < 1 || o.leaf_max > kMaxLeaves || (o.leaf_max & (o.leaf_max - 1)))
     return fail(LPA_EINVAL, "leaf_max = %d must be a power of two in [1, %d]", o.leaf_max, kMaxLeaves);
   if (((uintptr_t)indices & 15) != 0 || ((uintptr_t)weights & 15) != 0)
@@ -690,54 +761,64 @@ lpa_status plan_run(lpa_plan_s* p, double tol, int32_t max_iter, int32_t* labels
     return LPA_OK;
   }
   const bool timing = (p->flags & LPA_TIMING) != 0;
+  if (timing && (p->flags & LPA_GRAPH))
+    return fail(LPA_EINVAL, "LPA_GRAPH and LPA_TIMING cannot be combined");
   if (timing) {
     lpa_status es = ensure_events(p, 2 + 2 * (size_t)max_iter);
     if (es != LPA_OK) return es;
   }
-  LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));  // done, iterations, converged, err
-  LPA_CUDA(launch_fill_u64(p->dn, 0ull, (int64_t)max_iter * kDnSlots, s));
-  LPA_CUDA(launch_init_labels(labels_out, p->labels_in, n, s));
-  // pruning: act[0] = every vertex unprocessed before iteration 0; iteration l reads
-  // act[l & 1] and marks act[(l + 1) & 1]
   const bool prune = (p->flags & LPA_PRUNE) != 0;
-  uint8_t* act = (uint8_t*)(p->ws + p->lay.act);
-  unsigned long long* scanned = prune ? (unsigned long long*)(p->ws + p->lay.scanned) : nullptr;
-  unsigned long long* scan_total = (unsigned long long*)(p->ws + p->lay.scan_total);
-  if (prune) {
-    LPA_CUDA(launch_fill_u8(act, 1, n, s));
-    LPA_CUDA(launch_fill_u64(scanned, 0ull, (int64_t)max_iter * kDnSlots, s));
-  }
-  int32_t* buf[2] = {labels_out, p->tmp};
-  for (int l = 0; l < max_iter; ++l) {
-    const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
-    SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
-                             p->dn + (int64_t)l * kDnSlots, &p->st->done);
-    if (prune) {
-      a.act_in = act + (int64_t)(l & 1) * n;
-      a.act_out = act + (int64_t)((l + 1) & 1) * n;
-      a.scanned = scanned + (int64_t)l * kDnSlots;
-    }
-    if (timing) LPA_CUDA(cudaEventRecord(p->events[2 + 2 * l], s));
-    if (prune) LPA_CUDA(launch_fill_u8(a.act_out, 0, n, s));
-    LPA_CUDA(launch_one_sweep(p, a));
-    if (timing) LPA_CUDA(cudaEventRecord(p->events[3 + 2 * l], s));
-    LPA_CUDA(launch_converge(p->st, p->dn, p->dn_total, scanned, scan_total, l, pick_less, tol,
-                             n, s));
-  }
-  LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
   const bool want_q = (p->flags & LPA_MODULARITY) != 0;
-  if (want_q) {
-    LPA_CUDA(launch_plan_modularity(p, labels_out));
-    LPA_CUDA(cudaMemcpyAsync(p->host_q, p->ws + p->lay.out4, sizeof(double) * 4,
-                             cudaMemcpyDeviceToHost, s));
-  }
-  LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  if (max_iter > 0)
-    LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn_total, sizeof(unsigned long long) * max_iter,
-                             cudaMemcpyDeviceToHost, s));
-  if (max_iter > 0 && prune)
-    LPA_CUDA(cudaMemcpyAsync(p->host_scan, scan_total, sizeof(unsigned long long) * max_iter,
-                             cudaMemcpyDeviceToHost, s));
+  // every launch and copy of the run, stream-ordered on s with no host synchronisation
+  // (so that LPA_GRAPH can record it as one graph)
+  auto enqueue = [&](cudaStream_t s) -> lpa_status {
+    LPA_CUDA(launch_fill_i32((int32_t*)p->st, 0, 4, s));  // done, iterations, converged, err
+    LPA_CUDA(launch_fill_u64(p->dn, 0ull, (int64_t)max_iter * kDnSlots, s));
+    LPA_CUDA(launch_init_labels(labels_out, p->labels_in, n, s));
+    // pruning: act[0] = every vertex unprocessed before iteration 0; iteration l reads
+    // act[l & 1] and marks act[(l + 1) & 1]
+    uint8_t* act = (uint8_t*)(p->ws + p->lay.act);
+    unsigned long long* scanned = prune ? (unsigned long long*)(p->ws + p->lay.scanned) : nullptr;
+    unsigned long long* scan_total = (unsigned long long*)(p->ws + p->lay.scan_total);
+    if (prune) {
+      LPA_CUDA(launch_fill_u8(act, 1, n, s));
+      LPA_CUDA(launch_fill_u64(scanned, 0ull, (int64_t)max_iter * kDnSlots, s));
+    }
+    int32_t* buf[2] = {labels_out, p->tmp};
+    for (int l = 0; l < max_iter; ++l) {
+      const int pick_less = (p->rho > 0 && l % p->rho == 0) ? 1 : 0;
+      SweepArgs a = sweep_args(p, buf[l & 1], buf[(l + 1) & 1], pick_less,
+                               p->dn + (int64_t)l * kDnSlots, &p->st->done);
+      if (prune) {
+        a.act_in = act + (int64_t)(l & 1) * n;
+        a.act_out = act + (int64_t)((l + 1) & 1) * n;
+        a.scanned = scanned + (int64_t)l * kDnSlots;
+      }
+      if (timing) LPA_CUDA(cudaEventRecord(p->events[2 + 2 * l], s));
+      if (prune) LPA_CUDA(launch_fill_u8(a.act_out, 0, n, s));
+      LPA_CUDA(launch_one_sweep(p, a));
+      if (timing) LPA_CUDA(cudaEventRecord(p->events[3 + 2 * l], s));
+      LPA_CUDA(launch_converge(p->st, p->dn, p->dn_total, scanned, scan_total, l, pick_less, tol,
+                               n, s));
+    }
+    LPA_CUDA(launch_finalize(p->st, labels_out, p->tmp, n, s));
+    if (want_q) {
+      LPA_CUDA(launch_plan_modularity(p, labels_out));
+      LPA_CUDA(cudaMemcpyAsync(p->host_q, p->ws + p->lay.out4, sizeof(double) * 4,
+                               cudaMemcpyDeviceToHost, s));
+    }
+    LPA_CUDA(cudaMemcpyAsync(p->host_state, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    if (max_iter > 0)
+      LPA_CUDA(cudaMemcpyAsync(p->host_dn, p->dn_total, sizeof(unsigned long long) * max_iter,
+                               cudaMemcpyDeviceToHost, s));
+    if (max_iter > 0 && prune)
+      LPA_CUDA(cudaMemcpyAsync(p->host_scan, scan_total, sizeof(unsigned long long) * max_iter,
+                               cudaMemcpyDeviceToHost, s));
+    return LPA_OK;
+  };
+  const lpa_status es = (p->flags & LPA_GRAPH) ? run_recorded(p, labels_out, tol, max_iter, enqueue)
+                                              : enqueue(s);
+  if (es != LPA_OK) return es;
   LPA_CUDA(cudaStreamSynchronize(s));
   const int iters = p->host_state->iterations;
   if (iters < 0 || iters > max_iter) return fail(LPA_EINTERNAL, "device reported %d iterations", iters);
@@ -1519,7 +1600,10 @@ lpa_status lpa_batch_detect(const lpa_graph* graphs, int32_t count, lpa_mode mod
     return cleanup(fail(LPA_EUNSUPPORTED, "LPA_MODULARITY in a batch needs a sketch mode"));
   }
   if (st != LPA_OK) return cleanup(st);
-  st = batch_run(p, b, tol, max_iter);
+  st = (o.flags & LPA_GRAPH)
+           ? run_recorded(p, b.labels, tol, max_iter,
+                          [&](cudaStream_t) { return batch_run(p, b, tol, max_iter); })
+           : batch_run(p, b, tol, max_iter);
   const bool want_q = (o.flags & LPA_MODULARITY) != 0;
   double* d_q = (double*)(dev + o_q);
   if (st == LPA_OK && want_q && N > 0) {  // Eq. 1 per graph on the packed final labels

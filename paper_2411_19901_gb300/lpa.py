@@ -24,6 +24,7 @@ LPA_MODULARITY = 0x4
 LPA_PRUNE = 0x8
 LPA_MG_UNCLAMPED = 0x10
 LPA_RESCAN = 0x20
+LPA_GRAPH = 0x40
 LPA_MAX_ITER = 1024
 
 STATUS = {0: "LPA_OK", -1: "LPA_EINVAL", -2: "LPA_ENOMEM", -3: "LPA_ECUDA",
@@ -235,7 +236,7 @@ def lpa_options_init() -> lpa_options:
 def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=False,
                  modularity=False, labels_in=None, stream=None, workspace=None,
                  workspace_bytes=0, prune=False, unclamped=False, rescan=False,
-                 tuning=None) -> lpa_options:
+                 tuning=None, graph=False) -> lpa_options:
     """Options for the calls below.  ``tuning``: an lpa_tuning or a dict of its fields (the
     struct is kept alive by the returned options)."""
     o = lpa_options_init()
@@ -248,7 +249,8 @@ def make_options(pl_period=8, leaf_e0=64, leaf_max=256, validate=True, timing=Fa
     o.leaf_max = leaf_max
     o.flags = ((LPA_VALIDATE if validate else 0) | (LPA_TIMING if timing else 0)
                | (LPA_MODULARITY if modularity else 0) | (LPA_PRUNE if prune else 0)
-               | (LPA_MG_UNCLAMPED if unclamped else 0) | (LPA_RESCAN if rescan else 0))
+               | (LPA_MG_UNCLAMPED if unclamped else 0) | (LPA_RESCAN if rescan else 0)
+               | (LPA_GRAPH if graph else 0))
     o.labels_in = _ptr(labels_in)
     o.stream = _stream_handle(stream)
     if workspace is not None:

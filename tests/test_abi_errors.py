@@ -71,6 +71,12 @@ def test_option_checks(lpa):
         st, msg = status_of(lambda: lpa.lpa_detect_ex(fake, fake, None, 10, 5, mode, 8, 0.05, 20,
                                                       fake, None, o))
         assert st == EINVAL and "LPA_MG only" in msg
+    # a recorded graph cannot carry the per-sweep timing events
+    o = lpa.lpa_options_init()
+    o.flags |= lpa.LPA_TIMING | lpa.LPA_GRAPH
+    st, msg = status_of(lambda: lpa.lpa_detect_ex(fake, fake, None, 10, 5, "mg", 8, 0.05, 20,
+                                                  fake, None, o))
+    assert st == EINVAL and "LPA_GRAPH" in msg and "LPA_TIMING" in msg
 
 
 def test_batch_and_server_argument_checks(lpa):
