@@ -6,10 +6,16 @@ the modularity of the result -- one ``lpa_detect_ex`` call.  ``value`` is edges 
 per second (sum over steps of iterations * m, divided by the CUDA-event time of the
 timed steps).  ``e2e`` is the same metric through ``lpa_detect_host`` with the graph in
 page-locked host memory (host-to-device copy of the CSR and device-to-host copy of the
-labels inside the timed region).
+labels inside the timed region).  On the default workload the line also carries
+``forms``: short runs of the batched form (the first 256 graphs of the batched family,
+against one call per graph) and of the served form (the full arrival stream, 4000 timed
+requests, against first-in-first-out one-at-a-time solves), each with its own warm-up,
+timing and clock record (``--no-forms`` leaves them out).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload lfr26|rmat22|pp1000] [--mode mg|bm|exact]
+                  [--workload lfr26|rmat22|pp1000|lfr26s|lfr22|sbm256|sbm4096|serve]
+                  [--mode mg|bm|exact] [--k K] [--unclamped] [--rescan] [--tune]
+                  [--skip-cpu] [--no-forms]
 
 Under torchrun (N > 1) every rank solves its own replica (the single-graph path does not
 shard; scaling is weak) and rank 0 prints the line with the max time over ranks.
